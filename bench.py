@@ -1,0 +1,318 @@
+"""Benchmark: USTs sampled+aggregated per second and diag(L^+) wall time.
+
+One step = the whole path of Algorithm 1 on the R-MAT workload (scale 16,
+edge factor 16, a,b,c,d = 0.57,0.19,0.19,0.05, symmetrised, deduplicated,
+self-loops removed, largest component, max-degree pivot): BFS tree B_u,
+4096 Wilson trees with their Algorithm 2 counts, exact reduction into R, the
+FP32-PCG + FP64-refinement column solve and the FP64 diagonal. Inputs are
+resident on the device when a timed step starts; L2 is flushed (256 MB
+write) between timed steps, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. With N > 1 (torchrun, one rank per GPU) every rank
+samples its own 4096 trees (seed offset by rank; weak scaling), the integer
+counts are summed across ranks (the paper's final reduction of R) and the
+max step time over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "USTs sampled+aggregated/sec and diag(L†) wall time on 1 GB300; % of L2/HBM roofline"
+WORKLOAD = "rmat16"
+SEED = 0
+
+# Algorithmic bytes (what the method must touch, no cache effects):
+#   per Wilson draw: row_ptr pair 8 B + col_idx 4 B + successor write 4 B + stack depth 4 B
+#   per vertex per tree (intervals + aggregation bookkeeping): 40 B
+#   per pair test of Algorithm 2 (f^c(u) per tree): bfs_parent 4 B + successor 4 B + interval 8 B
+BYTES_PER_DRAW = 20
+BYTES_PER_VERTEX = 40
+BYTES_PER_PAIR = 16
+
+
+def algorithmic_bytes(draws: int, trees: int, n: int, farness: int) -> int:
+    return BYTES_PER_DRAW * draws + trees * (BYTES_PER_VERTEX * n + BYTES_PER_PAIR * farness)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p for p in vis.split(",") if p.strip()]
+    if parts and parts[min(local_rank, len(parts) - 1)].strip().isdigit():
+        return int(parts[min(local_rank, len(parts) - 1)])
+    return local_rank
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The oracle (plain C, OpenMP over trees) on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    g, u, T, _ = synth.workload(WORKLOAD)
+    threads = oracle.max_threads()
+    sample = T
+
+    def step():
+        ecc, dist, par = oracle.bfs(g, u)
+        R, _ = oracle.sample_aggregate(g, u, par, 0, sample, SEED, threads=threads)
+        x, _, _, _ = oracle.cg(g, u, tol=1e-9)
+        oracle.combine(R, sample, x, u)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    value = sample / sec
+    line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{WORKLOAD}: n={g.n} m={g.m} pivot={u} trees={sample} seed={SEED}",
+                       "sample": f"full workload: BFS + {sample} trees + FP64 CG + combine per step"},
+            "cpu_baseline": {"value": value, "unit": "trees/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} trees of the workload per step"},
+            "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(g, u, T) -> dict:
+    import oracle
+    threads = oracle.max_threads()
+    ecc, dist, par = oracle.bfs(g, u)
+    oracle.sample_aggregate(g, u, par, 0, 64, SEED, threads=threads)  # warm
+    t0 = time.perf_counter()
+    ecc, dist, par = oracle.bfs(g, u)
+    R, _ = oracle.sample_aggregate(g, u, par, 0, T, SEED, threads=threads)
+    x, _, _, _ = oracle.cg(g, u, tol=1e-9)
+    oracle.combine(R, T, x, u)
+    sec = time.perf_counter() - t0
+    return {"value": T / sec, "unit": "trees/s", "cores": threads, "kind": "oracle",
+            "sample": f"one full step ({T} trees + BFS + FP64 CG + combine), OpenMP over trees", "seconds": sec}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2006_13679_gb300 as pkg
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    pkg.build()
+    g, u, T, _ = synth.workload(WORKLOAD)
+    seed = SEED + rank
+    stream = torch.cuda.Stream()
+    rp_d = torch.from_numpy(g.row_ptr).cuda()
+    ci_d = torch.from_numpy(g.col_idx).cuda()
+    h = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True)
+    diag_d = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    counts_d = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        h.reset(u)                    # B_u, ecc, clear R
+        h.sample_aggregate(T, seed)   # Wilson + intervals + Algorithm 2 + exact reduction
+        if dist is not None:          # the paper's final reduction of R over ranks
+            h.counts(counts_d)
+            with torch.cuda.stream(stream):
+                dist.all_reduce(counts_d)
+        h.diag(0.0, diag_d)           # column solve + combination
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sample_ms, bfs_ms, solve_ms, draws = [], [], [], []
+    launches0 = h.info()["kernel_launches"]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index(local_rank)) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0[k].record(stream)
+            step()
+            ev1[k].record(stream)
+            inf = h.info()
+            sample_ms.append(inf["sample_ms"])
+            bfs_ms.append(inf["bfs_ms"])
+            solve_ms.append(inf["solve_ms"])
+            draws.append(inf["last_draws"])
+        torch.cuda.synchronize()
+    launches = h.info()["kernel_launches"] - launches0
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * T / (ms / 1e3)
+    clocks = clk.summary()
+
+    info = h.info()
+    kernel_ms = statistics.mean(sample_ms)
+    alg = algorithmic_bytes(int(statistics.mean(draws)), T, g.n, info["farness"])
+    peak, peak_kind = peaks()
+    achieved = alg / (kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sample_aggregate_kernel", "kernel_ms": kernel_ms,
+                "algorithmic_bytes": alg, "peak_kind": peak_kind}
+
+    # end to end through the public API with host buffers (validation included)
+    e2e_times = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with pkg.UST(g.row_ptr, g.col_idx, u) as he:
+            he.sample_aggregate(T, seed)
+            d_host = he.diag()
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_times.append(t1 - t0)
+    e2e_sec = statistics.mean(e2e_times)
+    h2d = (g.n + 1) * 4 + g.nnz * 4
+    d2h = g.n * 8
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(g, u, T)
+        line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": f"{WORKLOAD}: R-MAT scale 16, edge factor 16, LCC n={g.n} m={g.m}, "
+                                       f"max-degree pivot {u}, {T} trees per GPU, seed {SEED}+rank",
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads"},
+                "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,
+                                            "solve": statistics.mean(solve_ms)},
+                "draws_per_tree": statistics.mean(draws) / T, "cg_iters": info["cg_iters"],
+                "cg_refinements": info["cg_refinements"], "cg_relres": info["cg_relres"],
+                "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+                "gpu_launches_per_step": launches / args.steps,
+                "e2e": {"value": T / e2e_sec, "unit": "trees/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_sec * 1e3},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

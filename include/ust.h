@@ -1,0 +1,197 @@
+/*
+ * ust.h - C ABI of libust.so: GB300 (sm_103a) implementation of the UST
+ * approximation of diag(L^+) for a connected, undirected, unweighted graph
+ * (Angriman, Predari, van der Grinten, Meyerhenke, arXiv 2006.13679,
+ * Algorithm 1 "ApproxDiagLpinv").
+ *
+ * The library computes, on one GPU:
+ *   - the BFS tree B_u of the pivot u (Section 3.2, Algorithm 1),
+ *   - uniform spanning trees T_t rooted at u with Wilson's algorithm
+ *     (Appendix A.2), done as parallel cycle popping on per-vertex stacks,
+ *   - per tree, the +-1 electrical-flow counts of Algorithm 2 along the BFS
+ *     paths P(v), summed exactly into R[v] (an estimate of tau * r(u, v)),
+ *   - the column x = L^+[:, u] from L x = e_u - (1/n) 1, x _|_ 1
+ *     (Section 3.1 step 1, Algorithm 1), with FP32 Jacobi-PCG inside FP64
+ *     iterative refinement,
+ *   - diag(L^+): L^+[u,u] = x_u, L^+[v,v] = R[v]/tau - x_u + 2 x_v
+ *     (Eq. diag-comp, Algorithm 1).
+ *
+ * Random choices. Stack entry k of vertex v in tree t is the neighbour
+ *   col_idx[row_ptr[v] + floor(X * deg(v) / 2^64)],
+ * X = (w1 << 32) | w0 of Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (v, k, t, graph_id) and key (seed mod 2^32, seed >> 32). By Wilson's
+ * cycle-popping theorem the tree for (seed, t) does not depend on the order in
+ * which cycles are popped, so every tree, and therefore R, is a deterministic
+ * function of (graph, pivot, seed, tree ids), identical to a sequential
+ * loop-erased-walk implementation with the same stacks.
+ *
+ * Readings of the paper fixed by this library:
+ *   - Algorithm 2's subtree test is inclusive (v in the subtree of b, b
+ *     included); with the printed strict test the edge into v never counts.
+ *   - parent(.) in Algorithm 2 is the parent in T rooted at u.
+ *   - B_u's parent of v is the smallest-id neighbour one level closer to u.
+ *   - tau = ecc(u)^2 * ceil(ln(2m/delta) / (2 (1-kappa)^2 eps^2)), natural log.
+ *
+ * Conventions.
+ *   - All functions return UST_OK (0) or a negative UST_E* code; on error the
+ *     context keeps its previous committed state (R, tree count, column) and
+ *     ust_last_error() describes the failure.
+ *   - Host pointers are plain CPU memory; "device" pointers are CUDA device
+ *     pointers on the context's device. Every pointer argument is owned by
+ *     the caller; the library copies what it keeps.
+ *   - Work is issued on the context's stream (ust_opts.stream, a
+ *     cudaStream_t, or the legacy default stream when NULL). Functions that
+ *     return data to host memory synchronise that stream before returning.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef UST_H
+#define UST_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define UST_API __attribute__((visibility("default")))
+#else
+#define UST_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UST_OK 0
+#define UST_EINVAL (-1)        /* bad argument or malformed CSR (asymmetric, self-loop, unsorted/duplicate columns) */
+#define UST_ENOTCONNECTED (-2) /* graph is not connected */
+#define UST_ENOMEM (-3)        /* device or host allocation failed */
+#define UST_ECUDA (-4)         /* CUDA runtime error */
+#define UST_ETIMEOUT (-5)      /* a device loop hit its iteration bound (pop rounds, jump steps) */
+#define UST_ENOTCONVERGED (-6) /* the solver did not reach cg_tol within max_cg_iters */
+#define UST_ESTATE (-7)        /* call not valid in the context's state (e.g. no trees sampled) */
+
+typedef struct ust_ctx ust_ctx;
+
+/* Graph in CSR form, vertices 0..n-1. Row v lists the neighbours of v in
+ * strictly increasing order; every edge {a, b} appears as arc a->b and b->a.
+ * nnz = 2m. row_ptr has n+1 entries with row_ptr[0] = 0, row_ptr[n] = nnz.
+ * on_device = 1 when both arrays are device pointers. */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    int32_t on_device;
+} ust_csr;
+
+/* Options; zero-initialised fields take the defaults in brackets. */
+typedef struct {
+    double delta;           /* failure probability for tau [1/n] (Algorithm 1) */
+    double kappa;           /* error split between solver and sampling [0.3] (Appendix D.1) */
+    double cg_tol;          /* relative residual ||b - L x|| / ||b|| of the column [1e-9] */
+    int32_t max_pop_rounds; /* bound on cycle-popping rounds per tree [4*n + 64] */
+    int32_t max_cg_iters;   /* bound on inner FP32 PCG iterations per refinement step [20000] */
+    int32_t skip_validation; /* 1: trust the CSR; 0: check order, loops, symmetry on the host [0] */
+    int32_t graph_id;       /* fourth Philox counter word [0] */
+    int32_t block_threads;  /* threads per sampling CTA, 0 = tuned default */
+    int32_t ctas_per_sm;    /* sampling CTAs per SM, 0 = tuned default */
+    void *stream;           /* cudaStream_t to issue work on [NULL = legacy default stream] */
+} ust_opts;
+
+/* Counters of the committed state. */
+typedef struct {
+    int32_t n, nnz, pivot, ecc;
+    int64_t trees;          /* trees aggregated into R so far, ids [0, trees) */
+    uint64_t seed;          /* seed of the last sampling call */
+    int64_t draws;          /* stack entries drawn over all trees (Wilson walk steps) */
+    int64_t pop_rounds;     /* cycle-popping rounds summed over trees */
+    int32_t max_pop_rounds; /* largest number of rounds one tree needed */
+    int32_t max_tree_depth; /* largest depth of a sampled tree */
+    int64_t farness;        /* f^c(u) = sum_v dist(u, v): pair tests of Algorithm 2 per tree */
+    int32_t cg_iters;       /* inner PCG iterations of the last solve */
+    int32_t cg_refinements; /* FP64 refinement steps of the last solve */
+    double cg_relres;       /* final ||b - L x|| / ||b|| in FP64 */
+    int32_t sample_ctas;    /* CTAs of the sampling launch */
+    int32_t sample_threads; /* threads per sampling CTA */
+    int64_t kernel_launches; /* kernels this context has launched so far */
+    /* device time (CUDA events on the context's stream) of the last run of
+     * each phase, in milliseconds */
+    double bfs_ms;          /* B_u */
+    double sample_ms;       /* the sampling/aggregation kernel alone */
+    double reduce_ms;       /* summing the partial count rows */
+    double solve_ms;        /* the column solve */
+    double combine_ms;      /* the diagonal combination */
+    int64_t last_trees;     /* trees processed by the last sampling launch */
+    int64_t last_draws;     /* stack entries drawn by the last sampling launch */
+} ust_info;
+
+/* Fills *o with the defaults. */
+UST_API void ust_default_opts(ust_opts *o);
+
+/* Creates a context for graph g and pivot u = pivot: validates (unless
+ * skip_validation),
+ * copies the CSR to the device, computes B_u, ecc(u) and f^c(u).
+ * Errors: UST_EINVAL (bad CSR or pivot), UST_ENOTCONNECTED, UST_ENOMEM,
+ * UST_ECUDA. On error *out is NULL. */
+UST_API int ust_init(const ust_csr *g, int32_t pivot, const ust_opts *o, ust_ctx **out);
+
+/* Re-targets the context to pivot u = pivot on the same graph: recomputes
+ * B_u, ecc(u) and f^c(u) and clears R, the tree count and the cached column
+ * (Algorithm 1 from its first line). No allocation. Errors: UST_EINVAL,
+ * UST_ECUDA. */
+UST_API int ust_reset(ust_ctx *c, int32_t pivot);
+
+/* Samples trees with ids [trees, trees + n_trees) under `seed` and adds their
+ * Algorithm 2 counts to R (the sampling loop of Algorithm 1). Tree ids
+ * continue across calls, so k calls of n trees equal one call of k*n trees
+ * with the same seed. Tree ids must stay below 2^32. Errors: UST_EINVAL,
+ * UST_ETIMEOUT (a tree exceeded max_pop_rounds; R unchanged), UST_ECUDA. */
+UST_API int ust_sample_aggregate(ust_ctx *c, int64_t n_trees, uint64_t seed);
+
+/* Writes diag(L^+) estimates (n doubles) to diag_out (device pointer when
+ * out_on_device = 1). If eps > 0 and fewer than tau(eps) trees have been
+ * aggregated, first samples the missing ids with the last seed (seed 0 if
+ * none was given). Uses all aggregated trees: L^+[v,v] = R[v]/trees - x_u
+ * + 2 x_v, with x = L^+[:, u] solved once and cached. Errors: UST_ESTATE (no
+ * trees and eps <= 0), UST_ENOTCONVERGED, UST_ETIMEOUT, UST_ECUDA. */
+UST_API int ust_diag(ust_ctx *c, double eps, double *diag_out, int32_t out_on_device);
+
+/* Sample size tau(eps) of Algorithm 1 for this graph and pivot. */
+UST_API int64_t ust_tau(const ust_ctx *c, double eps);
+
+/* R[v] as exact integers (n int64). */
+UST_API int ust_get_counts(ust_ctx *c, int64_t *R_out, int32_t out_on_device);
+
+/* The column x = L^+[:, u] (n doubles); solves it first if needed. */
+UST_API int ust_get_column(ust_ctx *c, double *x_out, int32_t out_on_device);
+
+/* B_u on the host: parent[v] (-1 at u) and dist[v]; either may be NULL. */
+UST_API int ust_get_bfs(ust_ctx *c, int32_t *parent_out, int32_t *dist_out);
+
+/* Counts of trees [t0, t1) under `seed` written to R_out (n int64) without
+ * touching the context's R: parity checks on tree subsets. */
+UST_API int ust_tree_range_counts(ust_ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *R_out,
+                          int32_t out_on_device);
+
+/* The sampled trees themselves: for tree ids t0 .. t0+count-1 writes
+ * next_out[i*n + v] (tree parent of v, -1 at u) and, when pops_out is not
+ * NULL, pops_out[i*n + v] (cycles popped at v = stack depth of the final
+ * entry). Host pointers. */
+UST_API int ust_sample_trees(ust_ctx *c, int64_t t0, int32_t count, uint64_t seed, int32_t *next_out,
+                     int32_t *pops_out);
+
+/* Counters of the committed state. */
+UST_API int ust_get_info(const ust_ctx *c, ust_info *out);
+
+/* Static description of the last error of this context (never NULL). */
+UST_API const char *ust_last_error(const ust_ctx *c);
+
+/* Name of an error code. */
+UST_API const char *ust_strerror(int code);
+
+/* Releases every resource of the context; NULL is a no-op. */
+UST_API void ust_free(ust_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UST_H */

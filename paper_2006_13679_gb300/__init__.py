@@ -1,0 +1,164 @@
+"""GB300 (sm_103a) UST approximation of diag(L^+) (arXiv 2006.13679).
+
+The computation lives in libust.so (CUDA, C ABI in include/ust.h). This
+package builds it (``build()``) and wraps it: ``UST`` mirrors the C calls
+one to one and only marshals arguments. Host arguments are numpy arrays;
+device arguments are torch CUDA tensors (PyTorch supplies device memory and
+streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding
+from ._binding import (UST_EINVAL, UST_ENOMEM, UST_ENOTCONNECTED, UST_ENOTCONVERGED, UST_ESTATE,
+                       UST_ETIMEOUT, UST_OK, UstError, check, load)
+from ._build import LIB as LIB_PATH
+
+__all__ = ["UST", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
+           "UST_ENOMEM", "UST_ETIMEOUT", "UST_ENOTCONVERGED", "UST_ESTATE"]
+
+
+def build(force: bool = False) -> str:
+    """Compiles libust.so for sm_103a with nvcc (in-tree) and loads it."""
+    from . import _build
+    path = _build.build(force=force)
+    load()
+    return path
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, on_device) for a numpy array or a torch CUDA tensor."""
+    if _is_torch(x):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("device arguments must be contiguous CUDA tensors")
+        return ctypes.c_void_p(x.data_ptr()), 1
+    a = np.ascontiguousarray(x)
+    if a.dtype != dtype:
+        raise TypeError(f"expected {np.dtype(dtype).name}, got {a.dtype}")
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class UST:
+    """One graph and pivot: ``ust_init`` ... ``ust_free``.
+
+    row_ptr, col_idx: int32 CSR (numpy on the host or torch CUDA tensors),
+    symmetric, sorted rows, no self-loops, connected. pivot: the vertex u.
+    """
+
+    def __init__(self, row_ptr, col_idx, pivot: int, *, delta: float = 0.0, kappa: float = 0.3,
+                 cg_tol: float = 1e-9, max_pop_rounds: int = 0, max_cg_iters: int = 0, graph_id: int = 0,
+                 block_threads: int = 0, ctas_per_sm: int = 0, stream=None, skip_validation: bool = False):
+        L = load()
+        self._keep = []
+        rp = row_ptr if _is_torch(row_ptr) else np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = col_idx if _is_torch(col_idx) else np.ascontiguousarray(col_idx, dtype=np.int32)
+        self._keep += [rp, ci]
+        prp, dev_rp = _ptr(rp, np.int32)
+        pci, dev_ci = _ptr(ci, np.int32)
+        if dev_rp != dev_ci:
+            raise ValueError("row_ptr and col_idx must both be host or both be device arrays")
+        n = int(rp.shape[0]) - 1
+        g = _binding.ust_csr(n=n, nnz=int(ci.shape[0]), row_ptr=prp.value, col_idx=pci.value, on_device=dev_rp)
+        o = _binding.default_opts()
+        o.delta, o.kappa, o.cg_tol = delta, kappa, cg_tol
+        o.max_pop_rounds, o.max_cg_iters = max_pop_rounds, max_cg_iters
+        o.skip_validation = int(bool(skip_validation))
+        o.graph_id, o.block_threads, o.ctas_per_sm = graph_id, block_threads, ctas_per_sm
+        sh = _stream_handle(stream)
+        o.stream = sh.value if sh is not None else None
+        h = ctypes.c_void_p()
+        rc = L.ust_init(ctypes.byref(g), int(pivot), ctypes.byref(o), ctypes.byref(h))
+        check(rc, None)
+        self._h = h
+        self.n = n
+        self.pivot = int(pivot)
+
+    # -- lifecycle
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().ust_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def reset(self, pivot: int) -> None:
+        check(load().ust_reset(self._h, int(pivot)), self._h)
+        self.pivot = int(pivot)
+
+    def sample_aggregate(self, n_trees: int, seed: int) -> None:
+        check(load().ust_sample_aggregate(self._h, int(n_trees), int(seed) & (2 ** 64 - 1)), self._h)
+
+    def tau(self, eps: float) -> int:
+        return int(load().ust_tau(self._h, float(eps)))
+
+    def _out(self, out, dtype, count):
+        if out is None:
+            out = np.empty(count, dtype=dtype)
+        p, dev = _ptr(out, dtype)
+        return out, p, dev
+
+    def diag(self, eps: float = 0.0, out=None):
+        out, p, dev = self._out(out, np.float64, self.n)
+        check(load().ust_diag(self._h, float(eps), p, dev), self._h)
+        return out
+
+    def counts(self, out=None):
+        out, p, dev = self._out(out, np.int64, self.n)
+        check(load().ust_get_counts(self._h, p, dev), self._h)
+        return out
+
+    def column(self, out=None):
+        out, p, dev = self._out(out, np.float64, self.n)
+        check(load().ust_get_column(self._h, p, dev), self._h)
+        return out
+
+    def bfs(self):
+        par = np.empty(self.n, dtype=np.int32)
+        dist = np.empty(self.n, dtype=np.int32)
+        check(load().ust_get_bfs(self._h, ctypes.c_void_p(par.ctypes.data), ctypes.c_void_p(dist.ctypes.data)),
+              self._h)
+        return par, dist
+
+    def tree_range_counts(self, t0: int, t1: int, seed: int, out=None):
+        out, p, dev = self._out(out, np.int64, self.n)
+        check(load().ust_tree_range_counts(self._h, int(t0), int(t1), int(seed) & (2 ** 64 - 1), p, dev), self._h)
+        return out
+
+    def sample_trees(self, t0: int, count: int, seed: int, with_pops: bool = False):
+        nxt = np.empty((count, self.n), dtype=np.int32)
+        pops = np.empty((count, self.n), dtype=np.int32) if with_pops else None
+        check(load().ust_sample_trees(self._h, int(t0), int(count), int(seed) & (2 ** 64 - 1),
+                                      ctypes.c_void_p(nxt.ctypes.data),
+                                      ctypes.c_void_p(pops.ctypes.data) if with_pops else None), self._h)
+        return (nxt, pops) if with_pops else nxt
+
+    def info(self) -> dict:
+        i = _binding.ust_info()
+        check(load().ust_get_info(self._h, ctypes.byref(i)), self._h)
+        return i.as_dict()

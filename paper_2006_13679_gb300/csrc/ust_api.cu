@@ -1,0 +1,371 @@
+// C ABI entry points of libust.so (declared in include/ust.h).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ust_common.cuh"
+
+namespace ust {
+
+int fail(Ctx *c, int code, const std::string &msg)
+{
+    c->err = msg;
+    return code;
+}
+
+}  // namespace ust
+
+using ust::Ctx;
+
+namespace {
+
+thread_local std::string g_init_error = "no error";
+
+void release(Ctx *c)
+{
+    cudaFree(c->d_rp);
+    cudaFree(c->d_ci);
+    cudaFree(c->d_bpar);
+    cudaFree(c->d_dist);
+    cudaFree(c->d_flag);
+    cudaFree(c->d_ws);
+    cudaFree(c->d_Rp);
+    cudaFree(c->d_R);
+    cudaFree(c->d_Rtmp);
+    cudaFree(c->d_stats);
+    cudaFree(c->d_f32);
+    cudaFree(c->d_f64);
+    cudaFree(c->d_red);
+    cudaFree(c->d_x);
+    for (int i = 0; i < 2 * Ctx::kEvPhases; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->h_red) cudaFreeHost(c->h_red);
+}
+
+// Host checks of the CSR contract: row_ptr monotone from 0 to nnz, columns
+// in range and strictly increasing per row, no self-loops, every arc present
+// in both directions, no isolated vertex.
+int validate_csr(Ctx *c, int n, int nnz, const int32_t *rp, const int32_t *ci)
+{
+    if (rp[0] != 0 || rp[n] != nnz) return ust::fail(c, UST_EINVAL, "row_ptr must run from 0 to nnz");
+    for (int v = 0; v < n; ++v) {
+        const int b = rp[v], e = rp[v + 1];
+        if (e < b) return ust::fail(c, UST_EINVAL, "row_ptr is not monotone");
+        if (e == b) return ust::fail(c, UST_ENOTCONNECTED, "isolated vertex");
+        for (int k = b; k < e; ++k) {
+            const int w = ci[k];
+            if (w < 0 || w >= n) return ust::fail(c, UST_EINVAL, "column index out of range");
+            if (w == v) return ust::fail(c, UST_EINVAL, "self-loop");
+            if (k > b && ci[k - 1] >= w) return ust::fail(c, UST_EINVAL, "row not strictly increasing");
+            if (!std::binary_search(ci + rp[w], ci + rp[w + 1], v))
+                return ust::fail(c, UST_EINVAL, "CSR is not symmetric");
+        }
+    }
+    return UST_OK;
+}
+
+int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
+{
+    const int n = g->n, nnz = g->nnz;
+    c->n = n;
+    c->nnz = nnz;
+    c->pivot = pivot;
+    ust_opts def;
+    ust_default_opts(&def);
+    const ust_opts &op = o ? *o : def;
+    c->delta = op.delta > 0 ? op.delta : 1.0 / (double)n;
+    c->kappa = op.kappa > 0 ? op.kappa : 0.3;
+    c->cg_tol = op.cg_tol > 0 ? op.cg_tol : 1e-9;
+    c->max_pop_rounds = op.max_pop_rounds > 0 ? op.max_pop_rounds : (int)std::min<int64_t>(4ll * n + 64, 1 << 30);
+    c->max_cg_iters = op.max_cg_iters > 0 ? op.max_cg_iters : 20000;
+    c->graph_id = op.graph_id;
+    c->stream = reinterpret_cast<cudaStream_t>(op.stream);
+    UST_CUDA_TRY(cudaGetDevice(&c->device));
+    for (int i = 0; i < 2 * Ctx::kEvPhases; ++i) UST_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    UST_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+
+    if (!op.skip_validation) {
+        std::vector<int32_t> hrp, hci;
+        const int32_t *rp = g->row_ptr, *ci = g->col_idx;
+        if (g->on_device) {
+            hrp.resize((size_t)n + 1);
+            hci.resize((size_t)nnz);
+            UST_CUDA_TRY(cudaMemcpy(hrp.data(), g->row_ptr, hrp.size() * 4, cudaMemcpyDeviceToHost));
+            UST_CUDA_TRY(cudaMemcpy(hci.data(), g->col_idx, hci.size() * 4, cudaMemcpyDeviceToHost));
+            rp = hrp.data();
+            ci = hci.data();
+        }
+        const int rc = validate_csr(c, n, nnz, rp, ci);
+        if (rc) return rc;
+    }
+
+    if (cudaMalloc(&c->d_rp, ((size_t)n + 1) * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "row_ptr");
+    if (cudaMalloc(&c->d_ci, (size_t)nnz * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "col_idx");
+    const cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    UST_CUDA_TRY(cudaMemcpyAsync(c->d_rp, g->row_ptr, ((size_t)n + 1) * 4, kind, c->stream));
+    UST_CUDA_TRY(cudaMemcpyAsync(c->d_ci, g->col_idx, (size_t)nnz * 4, kind, c->stream));
+    if (cudaMalloc(&c->d_bpar, (size_t)n * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "bfs parent");
+    if (cudaMalloc(&c->d_dist, (size_t)n * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "bfs dist");
+    if (cudaMalloc(&c->d_flag, 64) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "flag");
+    if (cudaMalloc(&c->d_stats, 16 * sizeof(int64_t)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "stats");
+    if (cudaMallocHost(&c->h_stats, 16 * sizeof(int64_t)) != cudaSuccess)
+        return ust::fail(c, UST_ENOMEM, "pinned stats");
+    if (cudaMalloc(&c->d_R, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
+    if (cudaMalloc(&c->d_Rtmp, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)n * 8, c->stream));
+
+    int rc = ust::run_bfs(c);
+    if (rc) return rc;
+    rc = ust::alloc_sampler(c, op.block_threads, op.ctas_per_sm);
+    if (rc) return rc;
+    rc = ust::alloc_solver(c);
+    if (rc) return rc;
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return UST_OK;
+}
+
+int copy_out(Ctx *c, void *dst, const void *src, size_t bytes, int32_t on_device)
+{
+    if (!dst) return ust::fail(c, UST_EINVAL, "null output pointer");
+    UST_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+    if (!on_device) UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return UST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ust_default_opts(ust_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->kappa = 0.3;
+    o->cg_tol = 1e-9;
+}
+
+int ust_init(const ust_csr *g, int32_t pivot, const ust_opts *o, ust_ctx **out)
+{
+    if (!out) return UST_EINVAL;
+    *out = nullptr;
+    if (!g || !g->row_ptr || !g->col_idx || g->n < 2 || g->nnz < 2 || pivot < 0 || pivot >= g->n) {
+        g_init_error = "invalid graph or pivot (need n >= 2, nnz >= 2, 0 <= pivot < n)";
+        return UST_EINVAL;
+    }
+    ust_ctx *h = new (std::nothrow) ust_ctx;
+    if (!h) return UST_ENOMEM;
+    const int rc = init_impl(&h->c, g, pivot, o);
+    if (rc) {
+        g_init_error = h->c.err;
+        release(&h->c);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return UST_OK;
+}
+
+int ust_reset(ust_ctx *h, int32_t pivot)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (pivot < 0 || pivot >= c->n) return ust::fail(c, UST_EINVAL, "pivot out of range");
+    c->pivot = pivot;
+    c->trees = 0;
+    c->draws = 0;
+    c->pop_rounds = 0;
+    c->max_rounds_seen = 0;
+    c->max_depth_seen = 0;
+    c->x_valid = false;
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * 8, c->stream));
+    return ust::run_bfs(c);
+}
+
+int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (n_trees < 0) return ust::fail(c, UST_EINVAL, "n_trees < 0");
+    if (n_trees == 0) return UST_OK;
+    UST_CUDA_TRY(cudaMemcpyAsync(c->d_Rtmp, c->d_R, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    int64_t draws = 0, rounds = 0;
+    int max_rounds = 0, max_depth = 0;
+    const int rc = ust::run_sampler(c, c->trees, c->trees + n_trees, seed, c->d_Rtmp, nullptr, nullptr, &draws,
+                                    &rounds, &max_rounds, &max_depth);
+    if (rc) return rc;
+    std::swap(c->d_R, c->d_Rtmp);
+    c->trees += n_trees;
+    c->seed = seed;
+    c->draws += draws;
+    c->pop_rounds += rounds;
+    c->max_rounds_seen = std::max(c->max_rounds_seen, max_rounds);
+    c->max_depth_seen = std::max(c->max_depth_seen, max_depth);
+    return UST_OK;
+}
+
+int64_t ust_tau(const ust_ctx *h, double eps)
+{
+    if (!h || !(eps > 0)) return 0;
+    const Ctx *c = &h->c;
+    const double m = (double)c->nnz / 2.0;
+    const double a = log(2.0 * m / c->delta);
+    const double b = 2.0 * (1.0 - c->kappa) * (1.0 - c->kappa) * eps * eps;
+    return (int64_t)c->ecc * (int64_t)c->ecc * (int64_t)ceil(a / b);
+}
+
+int ust_diag(ust_ctx *h, double eps, double *diag_out, int32_t out_on_device)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (!diag_out) return ust::fail(c, UST_EINVAL, "null output pointer");
+    if (eps > 0) {
+        const int64_t tau = ust_tau(h, eps);
+        if (c->trees < tau) {
+            const int rc = ust_sample_aggregate(h, tau - c->trees, c->seed);
+            if (rc) return rc;
+        }
+    }
+    if (c->trees <= 0) return ust::fail(c, UST_ESTATE, "no trees aggregated");
+    if (!c->x_valid) {
+        const int rc = ust::run_solve(c);
+        if (rc) return rc;
+    }
+    double *dst = out_on_device ? diag_out : c->d_f64 + c->n;
+    int rc = ust::run_combine(c, c->trees, dst);
+    if (rc) return rc;
+    if (!out_on_device) return copy_out(c, diag_out, dst, (size_t)c->n * 8, 0);
+    return UST_OK;
+}
+
+int ust_get_counts(ust_ctx *h, int64_t *R_out, int32_t out_on_device)
+{
+    if (!h) return UST_EINVAL;
+    return copy_out(&h->c, R_out, h->c.d_R, (size_t)h->c.n * 8, out_on_device);
+}
+
+int ust_get_column(ust_ctx *h, double *x_out, int32_t out_on_device)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (!c->x_valid) {
+        const int rc = ust::run_solve(c);
+        if (rc) return rc;
+    }
+    return copy_out(c, x_out, c->d_x, (size_t)c->n * 8, out_on_device);
+}
+
+int ust_get_bfs(ust_ctx *h, int32_t *parent_out, int32_t *dist_out)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (parent_out) {
+        const int rc = copy_out(c, parent_out, c->d_bpar, (size_t)c->n * 4, 0);
+        if (rc) return rc;
+    }
+    if (dist_out) return copy_out(c, dist_out, c->d_dist, (size_t)c->n * 4, 0);
+    return UST_OK;
+}
+
+int ust_tree_range_counts(ust_ctx *h, int64_t t0, int64_t t1, uint64_t seed, int64_t *R_out, int32_t out_on_device)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (!R_out || t0 < 0 || t1 < t0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_Rtmp, 0, (size_t)c->n * 8, c->stream));
+    const int rc = ust::run_sampler(c, t0, t1, seed, c->d_Rtmp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    return copy_out(c, R_out, c->d_Rtmp, (size_t)c->n * 8, out_on_device);
+}
+
+int ust_sample_trees(ust_ctx *h, int64_t t0, int32_t count, uint64_t seed, int32_t *next_out, int32_t *pops_out)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (!next_out || count < 0 || t0 < 0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
+    if (count == 0) return UST_OK;
+    const size_t elems = (size_t)count * (size_t)c->n;
+    int32_t *d_next = nullptr, *d_pops = nullptr;
+    if (cudaMalloc(&d_next, elems * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "tree export buffer");
+    if (pops_out && cudaMalloc(&d_pops, elems * 4) != cudaSuccess) {
+        cudaFree(d_next);
+        return ust::fail(c, UST_ENOMEM, "tree export buffer");
+    }
+    int rc = ust::run_sampler(c, t0, t0 + count, seed, nullptr, d_next, d_pops, nullptr, nullptr, nullptr, nullptr);
+    if (!rc) rc = copy_out(c, next_out, d_next, elems * 4, 0);
+    if (!rc && pops_out) rc = copy_out(c, pops_out, d_pops, elems * 4, 0);
+    cudaFree(d_next);
+    cudaFree(d_pops);
+    return rc;
+}
+
+int ust_get_info(const ust_ctx *h, ust_info *out)
+{
+    if (!h || !out) return UST_EINVAL;
+    const Ctx *c = &h->c;
+    memset(out, 0, sizeof(*out));
+    out->n = c->n;
+    out->nnz = c->nnz;
+    out->pivot = c->pivot;
+    out->ecc = c->ecc;
+    out->trees = c->trees;
+    out->seed = c->seed;
+    out->draws = c->draws;
+    out->pop_rounds = c->pop_rounds;
+    out->max_pop_rounds = c->max_rounds_seen;
+    out->max_tree_depth = c->max_depth_seen;
+    out->farness = c->farness;
+    out->cg_iters = c->cg_iters;
+    out->cg_refinements = c->cg_refinements;
+    out->cg_relres = c->cg_relres;
+    out->sample_ctas = c->ctas;
+    out->sample_threads = c->block_threads;
+    out->kernel_launches = c->launches;
+    out->last_trees = c->last_trees;
+    out->last_draws = c->last_draws;
+    double *ms[Ctx::kEvPhases] = {&out->bfs_ms, &out->sample_ms, &out->reduce_ms, &out->solve_ms, &out->combine_ms};
+    for (int ph = 0; ph < Ctx::kEvPhases; ++ph) {
+        if (!c->ev_used[ph]) continue;
+        float t = 0.0f;
+        if (cudaEventSynchronize(c->ev[2 * ph + 1]) != cudaSuccess) return UST_ECUDA;
+        if (cudaEventElapsedTime(&t, c->ev[2 * ph], c->ev[2 * ph + 1]) != cudaSuccess) return UST_ECUDA;
+        *ms[ph] = (double)t;
+    }
+    return UST_OK;
+}
+
+const char *ust_last_error(const ust_ctx *h)
+{
+    if (!h) return g_init_error.c_str();
+    return h->c.err.empty() ? "no error" : h->c.err.c_str();
+}
+
+const char *ust_strerror(int code)
+{
+    switch (code) {
+    case UST_OK: return "UST_OK";
+    case UST_EINVAL: return "UST_EINVAL";
+    case UST_ENOTCONNECTED: return "UST_ENOTCONNECTED";
+    case UST_ENOMEM: return "UST_ENOMEM";
+    case UST_ECUDA: return "UST_ECUDA";
+    case UST_ETIMEOUT: return "UST_ETIMEOUT";
+    case UST_ENOTCONVERGED: return "UST_ENOTCONVERGED";
+    case UST_ESTATE: return "UST_ESTATE";
+    default: return "UST_E?";
+    }
+}
+
+void ust_free(ust_ctx *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->c.stream);
+    release(&h->c);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// BFS tree B_u of the pivot (Section 3.2, Algorithm 1).
+//
+// Level-synchronous bottom-up ("pull") BFS: at level L every unvisited
+// vertex scans its sorted adjacency row and stops at the first neighbour at
+// distance L. Because rows are sorted, that neighbour is the smallest-id
+// vertex one level closer to u, which is the parent rule of B_u.
+#include "ust_common.cuh"
+
+namespace ust {
+namespace {
+
+__global__ void bfs_init_kernel(int n, int u, int32_t *__restrict__ dist, int32_t *__restrict__ bpar)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        dist[v] = (v == u) ? 0 : -1;
+        bpar[v] = -1;
+    }
+}
+
+__global__ void bfs_pull_kernel(int n, int level, const int32_t *__restrict__ rp,
+                                const int32_t *__restrict__ ci, int32_t *dist,
+                                int32_t *__restrict__ bpar, int32_t *__restrict__ found)
+{
+    int any = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (dist[v] >= 0) continue;
+        const int e1 = __ldg(rp + v + 1);
+        for (int e = __ldg(rp + v); e < e1; ++e) {
+            const int w = __ldg(ci + e);
+            if (dist[w] == level) {
+                dist[v] = level + 1;
+                bpar[v] = w;
+                any = 1;
+                break;
+            }
+        }
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) *found = 1;
+}
+
+// stats[0] += sum of dist, stats[1] += number of unreached vertices
+__global__ void bfs_sum_kernel(int n, const int32_t *__restrict__ dist, unsigned long long *stats)
+{
+    long long s = 0, bad = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int d = dist[v];
+        if (d < 0) bad += 1; else s += d;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(stats + 0, (unsigned long long)s);
+        atomicAdd(stats + 1, (unsigned long long)bad);
+    }
+}
+
+}  // namespace
+
+int run_bfs(Ctx *c)
+{
+    const int n = c->n;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    phase_begin(c, Ctx::kEvBfs);
+    bfs_init_kernel<<<blocks, threads, 0, c->stream>>>(n, c->pivot, c->d_dist, c->d_bpar);
+    c->launches += 1;
+    UST_CUDA_TRY(cudaGetLastError());
+    int32_t *h_found = reinterpret_cast<int32_t *>(c->h_stats);
+    int level = 0;
+    for (;; ++level) {
+        if (level > n) return fail(c, UST_ETIMEOUT, "BFS did not terminate");
+        UST_CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, sizeof(int32_t), c->stream));
+        bfs_pull_kernel<<<blocks, threads, 0, c->stream>>>(n, level, c->d_rp, c->d_ci, c->d_dist,
+                                                           c->d_bpar, c->d_flag);
+        c->launches += 1;
+        UST_CUDA_TRY(cudaGetLastError());
+        UST_CUDA_TRY(cudaMemcpyAsync(h_found, c->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (*h_found == 0) break;
+    }
+    c->ecc = level;
+    unsigned long long *d_sum = reinterpret_cast<unsigned long long *>(c->d_stats);
+    UST_CUDA_TRY(cudaMemsetAsync(d_sum, 0, 2 * sizeof(unsigned long long), c->stream));
+    bfs_sum_kernel<<<blocks, threads, 0, c->stream>>>(n, c->d_dist, d_sum);
+    c->launches += 1;
+    phase_end(c, Ctx::kEvBfs);
+    UST_CUDA_TRY(cudaGetLastError());
+    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, d_sum, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->h_stats[1] != 0) return fail(c, UST_ENOTCONNECTED, "graph is not connected");
+    c->farness = c->h_stats[0];
+    return UST_OK;
+}
+
+}  // namespace ust

@@ -1,0 +1,114 @@
+// Shared declarations of libust.so (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "ust.h"
+
+#define UST_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            return ust::fail(c, UST_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+        }                                                                           \
+    } while (0)
+
+namespace ust {
+
+// Device status word bits (written by kernels, read by the host).
+enum : int {
+    kStatusPopRounds = 1,  // a tree exceeded max_pop_rounds
+    kStatusJumpSteps = 2,  // pointer jumping did not converge within its bound
+    kStatusBadState = 4,   // an internal consistency check failed
+};
+
+// Per-CTA scratch of the sampling kernel: `kWsArrays` int32 arrays of
+// `stride` entries each, laid out array-major inside one CTA slot.
+constexpr int kWsArrays = 11;
+
+struct Ctx {
+    int n = 0;
+    int nnz = 0;
+    int pivot = 0;
+    int graph_id = 0;
+    int ecc = 0;
+    int64_t farness = 0;
+    double delta = 0, kappa = 0.3, cg_tol = 1e-9;
+    int max_pop_rounds = 0;
+    int max_cg_iters = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+
+    // graph and B_u
+    int32_t *d_rp = nullptr, *d_ci = nullptr;
+    int32_t *d_bpar = nullptr, *d_dist = nullptr;
+    int32_t *d_flag = nullptr;  // BFS level flag and misc small device scalars
+
+    // sampling
+    int block_threads = 0, ctas = 0;
+    int64_t ws_stride = 0;
+    int32_t *d_ws = nullptr;    // ctas * kWsArrays * ws_stride
+    int32_t *d_Rp = nullptr;    // ctas * n partial counts
+    int64_t *d_R = nullptr;     // committed counts
+    int64_t *d_Rtmp = nullptr;  // scratch counts (uncommitted)
+    int64_t *d_stats = nullptr; // [0] draws, [1] rounds, [2] max rounds, [3] max depth, [4] next tree, [5] status
+    int64_t *h_stats = nullptr; // pinned mirror
+
+    // solve
+    float *d_f32 = nullptr;     // inner PCG vectors
+    double *d_f64 = nullptr;    // outer vectors
+    double *d_red = nullptr;    // reduction partials
+    double *h_red = nullptr;    // pinned scalars
+    double *d_x = nullptr;      // column L^+[:, u]
+    bool x_valid = false;
+    int solve_blocks = 0;
+
+    // phase timers: event pairs for bfs, sample kernel, reduce, solve, combine
+    enum { kEvBfs = 0, kEvSample = 1, kEvReduce = 2, kEvSolve = 3, kEvCombine = 4, kEvPhases = 5 };
+    cudaEvent_t ev[2 * kEvPhases] = {};
+    bool ev_used[kEvPhases] = {};
+    int64_t launches = 0;
+    int64_t last_trees = 0, last_draws = 0;
+
+    // committed state
+    int64_t trees = 0;
+    uint64_t seed = 0;
+    int64_t draws = 0, pop_rounds = 0;
+    int max_rounds_seen = 0, max_depth_seen = 0;
+    int cg_iters = 0, cg_refinements = 0;
+    double cg_relres = 0;
+
+    std::string err;
+};
+
+int fail(Ctx *c, int code, const std::string &msg);
+
+// Records the start / end event of a timed phase on the context's stream.
+inline void phase_begin(Ctx *c, int ph) { cudaEventRecord(c->ev[2 * ph], c->stream); }
+inline void phase_end(Ctx *c, int ph)
+{
+    cudaEventRecord(c->ev[2 * ph + 1], c->stream);
+    c->ev_used[ph] = true;
+}
+
+// Host drivers (one per translation unit).
+int run_bfs(Ctx *c);
+int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm);
+// mode 0: aggregate trees [t0, t1) into d_out (int64 n) - added, not assigned.
+// mode 1: export next/pops of trees [t0, t1) to device buffers.
+int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
+                int32_t *d_pops_out, int64_t *draws, int64_t *rounds, int *max_rounds, int *max_depth);
+int alloc_solver(Ctx *c);
+int run_solve(Ctx *c);
+int run_combine(Ctx *c, int64_t tau, double *d_diag);
+
+}  // namespace ust
+
+struct ust_ctx {
+    ust::Ctx c;
+};

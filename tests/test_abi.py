@@ -1,0 +1,70 @@
+"""The C ABI library loads and exports every entry point include/ust.h
+declares; argument checks that need no GPU. No compute calls here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ust.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*UST_API\s+(?:const\s+)?[a-z_0-9]+\s*\*?\s*(ust_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2006_13679_gb300 as pkg
+    pkg.build()
+    return pkg.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ust_init", "ust_sample_aggregate", "ust_diag", "ust_free"]:
+        assert required in names
+    assert len(names) >= 14
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2006_13679_gb300 import _binding
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _binding.EXPORTS, name
+
+
+def test_binding_structs_match_header_layout(lib):
+    from paper_2006_13679_gb300 import _binding
+    # ust_opts: 3 doubles, 6 int32, pointer -> 3*8 + 6*4 + 8 = 56 bytes
+    assert ctypes.sizeof(_binding.ust_opts) == 56
+    assert ctypes.sizeof(_binding.ust_csr) == 32  # 2 int32, 2 pointers, int32 + padding
+    o = _binding.default_opts()
+    assert o.kappa == 0.3 and o.cg_tol == 1e-9 and o.skip_validation == 0
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
+    from paper_2006_13679_gb300 import _binding
+    h = ctypes.c_void_p()
+    g = _binding.ust_csr(n=1, nnz=0, row_ptr=None, col_idx=None, on_device=0)
+    assert lib.ust_init(ctypes.byref(g), 0, None, ctypes.byref(h)) == _binding.UST_EINVAL
+    assert h.value is None
+    assert b"n >= 2" in lib.ust_last_error(None)
+    assert lib.ust_strerror(-5) == b"UST_ETIMEOUT"
+    lib.ust_free(None)
+    assert lib.ust_tau(None, 0.3) == 0
+
+
+def test_product_package_does_not_import_the_oracle():
+    import subprocess
+    import sys
+    code = ("import sys, paper_2006_13679_gb300 as p; p.load(); "
+            "assert 'oracle' not in sys.modules, 'product imported oracle'")
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
+    # the CUDA sources never mention the oracle's C entry points
+    csrc = os.path.join(ROOT, "paper_2006_13679_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "orc_" not in open(os.path.join(csrc, f)).read(), f

@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work (B_u, sampled trees, pop counts, R) must match bit for bit.
+Floating point: the column x = L^+[:, u] within 1e-8 of an FP64 reference
+(dense pseudoinverse or FP64 CG at 1e-13); the diagonal within 1e-12
+relative of the oracle's combination applied to the same R and x.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+COL_TOL = 1e-8     # column vs FP64 reference, absolute, scaled by max(1, |x|_inf)
+DIAG_RTOL = 1e-12  # diag vs oracle combine on the same (R, x)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2006_13679_gb300 as p
+    p.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.lib()
+    return oracle
+
+
+def make(pkg, g, u, **kw):
+    return pkg.UST(g.row_ptr, g.col_idx, u, **kw)
+
+
+GRAPHS = {
+    "grid48": lambda: (synth.grid(48, 48), 24 * 48 + 24),
+    "rmat12": lambda: (lambda g: (g, synth.max_degree_vertex(g)))(synth.rmat(12, 16, seed=5)),
+    "ba3000": lambda: (lambda g: (g, synth.max_degree_vertex(g)))(synth.ba(3000, 4, seed=2)),
+    "er2000": lambda: (lambda g: (g, synth.max_degree_vertex(g)))(synth.er(2000, 6.0, seed=3)),
+    "path50": lambda: (synth.path(50), 17),
+    "k2": lambda: (synth.path(2), 1),
+}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_bfs_tree(pkg, orc, name):
+    g, u = GRAPHS[name]()
+    with make(pkg, g, u) as h:
+        par, dist = h.bfs()
+        ecc, d_ref, p_ref = orc.bfs(g, u)
+        assert np.array_equal(dist, d_ref)
+        assert np.array_equal(par, p_ref)
+        info = h.info()
+        assert info["ecc"] == ecc
+        assert info["farness"] == int(d_ref.astype(np.int64).sum())
+
+
+@pytest.mark.parametrize("name", ["grid48", "rmat12", "ba3000", "er2000"])
+def test_sampled_trees_bit_exact(pkg, orc, name):
+    """Every sampled tree and every per-vertex pop count equals the
+    sequential loop-erased-walk tree on the same stacks."""
+    g, u = GRAPHS[name]()
+    seed = 0x1234_5678_9ABC_DEF0
+    with make(pkg, g, u) as h:
+        nxt, pops = h.sample_trees(3, 40, seed, with_pops=True)
+        for i in range(40):
+            ref, ref_pops, _ = orc.wilson(g, u, 3 + i, seed)
+            assert np.array_equal(nxt[i], ref), (name, i)
+            assert np.array_equal(pops[i], ref_pops), (name, i)
+
+
+def test_counts_grid48_full(pkg, orc):
+    """48x48 grid, pivot 1176, 1000 trees, seed 0: R bit-exact."""
+    g, u = GRAPHS["grid48"]()
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(1000, 0)
+        R = h.counts()
+        _, _, par = orc.bfs(g, u)
+        R_ref, steps = orc.sample_aggregate(g, u, par, 0, 1000, 0, threads=THREADS)
+        assert np.array_equal(R, R_ref)
+        info = h.info()
+        assert info["trees"] == 1000 and info["draws"] == steps
+
+
+def test_counts_rmat16_full(pkg, orc):
+    """R-MAT scale 16, edge factor 16, LCC, max-degree pivot, 4096 trees, in
+    the sampler's default launch configuration: R bit-exact."""
+    g, u, T, _ = synth.workload("rmat16")
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(T, 0)
+        R = h.counts()
+        _, _, par = orc.bfs(g, u)
+        R_ref, steps = orc.sample_aggregate(g, u, par, 0, T, 0, threads=THREADS)
+        assert np.array_equal(R, R_ref)
+        assert h.info()["draws"] == steps
+
+
+def test_calls_continue_tree_ids(pkg, orc):
+    g = synth.grid(7, 5)
+    u = 17
+    with make(pkg, g, u) as a, make(pkg, g, u) as b:
+        a.sample_aggregate(37, 9)
+        for k in (1, 5, 31):
+            b.sample_aggregate(k, 9)
+        assert np.array_equal(a.counts(), b.counts())
+        assert a.info()["trees"] == b.info()["trees"] == 37
+        _, _, par = orc.bfs(g, u)
+        R_ref, _ = orc.sample_aggregate(g, u, par, 0, 37, 9)
+        assert np.array_equal(a.counts(), R_ref)
+        # a tree range that does not start at 0
+        assert np.array_equal(a.tree_range_counts(5, 36, 9), orc.sample_aggregate(g, u, par, 5, 36, 9)[0])
+
+
+@pytest.mark.parametrize("maker,u", [(lambda: synth.path(2), 0), (lambda: synth.path(31), 0),
+                                     (lambda: synth.star(20), 0), (lambda: synth.star(20), 7),
+                                     (lambda: synth.complete(9), 4), (lambda: synth.cycle(13), 12),
+                                     (lambda: synth.grid(1, 40), 39)])
+def test_edge_graphs(pkg, orc, maker, u):
+    g = maker()
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(301, 77)
+        _, dist, par = orc.bfs(g, u)
+        R_ref, _ = orc.sample_aggregate(g, u, par, 0, 301, 77)
+        assert np.array_equal(h.counts(), R_ref)
+        if g.m == g.n - 1:  # a tree: every UST is G itself
+            assert np.array_equal(h.counts(), 301 * dist.astype(np.int64))
+
+
+@pytest.mark.parametrize("bt,cps", [(256, 1), (256, 8), (512, 2), (1024, 1)])
+def test_launch_configurations_agree(pkg, orc, bt, cps):
+    g, u = GRAPHS["rmat12"]()
+    with make(pkg, g, u, block_threads=bt, ctas_per_sm=cps) as h:
+        h.sample_aggregate(500, 3)
+        _, _, par = orc.bfs(g, u)
+        R_ref, _ = orc.sample_aggregate(g, u, par, 0, 500, 3, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+
+
+def test_column_and_diag_grid48(pkg, orc):
+    g, u = GRAPHS["grid48"]()
+    Lp = orc.dense_pinv(g)
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(1000, 0)
+        x = h.column()
+        assert np.max(np.abs(x - Lp[:, u])) <= COL_TOL * max(1.0, np.max(np.abs(Lp[:, u])))
+        assert abs(x.sum()) < 1e-9
+        info = h.info()
+        assert info["cg_relres"] <= 1e-9
+        d = h.diag()
+        R = h.counts()
+        ref = orc.combine(R, 1000, x, u)
+        np.testing.assert_allclose(d, ref, rtol=DIAG_RTOL, atol=0)
+        # within the Hoeffding guarantee of tau = 1000 trees (Theorem 2)
+        ecc = info["ecc"]
+        eps_tau = ecc * np.sqrt(np.log(2 * g.m * g.n) / (2 * 1000)) / (1 - 0.3)
+        assert np.max(np.abs(d - np.diag(Lp))) <= eps_tau
+
+
+def test_column_rmat16_against_fp64_cg(pkg, orc):
+    g, u, T, _ = synth.workload("rmat16")
+    with make(pkg, g, u) as h:
+        x = h.column()
+        x_ref, _, rr, ok = orc.cg(g, u, tol=1e-13)
+        assert ok
+        assert np.max(np.abs(x - x_ref)) <= COL_TOL * max(1.0, np.max(np.abs(x_ref)))
+        assert h.info()["cg_relres"] <= 1e-9
+
+
+def test_diag_tops_up_to_tau(pkg, orc):
+    g = synth.grid(10, 10)
+    u = 55
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(10, 4)
+        tau = h.tau(2.0)
+        ecc, _, _ = orc.bfs(g, u)
+        assert tau == orc.tau(ecc, g.m, 2.0, 1.0 / g.n, 0.3)
+        d = h.diag(2.0)
+        assert h.info()["trees"] == tau
+        np.testing.assert_allclose(d, orc.combine(h.counts(), tau, h.column(), u), rtol=DIAG_RTOL, atol=0)
+        Lp = orc.dense_pinv(g)
+        assert np.max(np.abs(d - np.diag(Lp))) <= 2.0
+
+
+def test_error_paths(pkg):
+    from paper_2006_13679_gb300 import UstError, UST_ENOTCONNECTED, UST_EINVAL, UST_ESTATE, UST_ETIMEOUT
+    g = synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], lcc=False)
+    with pytest.raises(UstError) as e:
+        make(pkg, g, 0)
+    assert e.value.code == UST_ENOTCONNECTED
+    rp = np.array([0, 1, 2, 2], dtype=np.int32)  # arc 0->1, 1->2 without reverses
+    ci = np.array([1, 2], dtype=np.int32)
+    with pytest.raises(UstError) as e:
+        pkg.UST(rp, ci, 0)
+    assert e.value.code in (UST_EINVAL, UST_ENOTCONNECTED)
+    g, u = GRAPHS["grid48"]()
+    with make(pkg, g, u) as h:
+        with pytest.raises(UstError) as e:
+            h.diag()
+        assert e.value.code == UST_ESTATE
+    with make(pkg, g, u, max_pop_rounds=1) as h:
+        with pytest.raises(UstError) as e:
+            h.sample_aggregate(8, 0)
+        assert e.value.code == UST_ETIMEOUT
+        assert h.info()["trees"] == 0
+        assert not h.counts().any()
+
+
+def test_device_pointers(pkg, orc):
+    import torch
+    g, u = GRAPHS["rmat12"]()
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    st = torch.cuda.Stream()
+    with pkg.UST(rp, ci, u, stream=st) as h:
+        h.sample_aggregate(200, 1)
+        R = torch.empty(g.n, dtype=torch.int64, device="cuda")
+        h.counts(R)
+        d = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        h.diag(0.0, d)
+        st.synchronize()
+        _, _, par = orc.bfs(g, u)
+        R_ref, _ = orc.sample_aggregate(g, u, par, 0, 200, 1)
+        assert np.array_equal(R.cpu().numpy(), R_ref)
+        x = h.column()
+        np.testing.assert_allclose(d.cpu().numpy(), orc.combine(R_ref, 200, x, u), rtol=DIAG_RTOL, atol=0)
+
+
+def test_repeat_runs_are_identical(pkg):
+    g, u = GRAPHS["ba3000"]()
+    with make(pkg, g, u) as a, make(pkg, g, u) as b:
+        a.sample_aggregate(300, 11)
+        b.sample_aggregate(300, 11)
+        assert np.array_equal(a.counts(), b.counts())
+        assert np.array_equal(a.diag(), b.diag())
