@@ -87,7 +87,7 @@ typedef struct {
     double delta;           /* failure probability for tau [1/n] (Algorithm 1) */
     double kappa;           /* error split between solver and sampling [0.3] (Appendix D.1) */
     double cg_tol;          /* relative residual ||b - L x|| / ||b|| of the column [1e-9] */
-    int32_t max_pop_rounds; /* bound on cycle-popping rounds per tree [4*n + 64] */
+    int32_t max_pop_rounds; /* bound on cycle-popping rounds per tree [16 (2m ecc(u) + n) + 1024] */
     int32_t max_cg_iters;   /* bound on inner FP32 PCG iterations per refinement step [20000] */
     int32_t skip_validation; /* 1: trust the CSR; 0: check order, loops, symmetry on the host [0] */
     int32_t graph_id;       /* fourth Philox counter word [0] */
@@ -104,7 +104,7 @@ typedef struct {
     int64_t draws;          /* stack entries drawn over all trees (Wilson walk steps) */
     int64_t pop_rounds;     /* cycle-popping rounds summed over trees */
     int32_t max_pop_rounds; /* largest number of rounds one tree needed */
-    int32_t max_tree_depth; /* largest depth of a sampled tree */
+    int32_t max_round_pops; /* most vertices popped in one cycle-popping round */
     int64_t farness;        /* f^c(u) = sum_v dist(u, v): pair tests of Algorithm 2 per tree */
     int32_t cg_iters;       /* inner PCG iterations of the last solve */
     int32_t cg_refinements; /* FP64 refinement steps of the last solve */

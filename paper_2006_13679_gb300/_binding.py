@@ -40,7 +40,7 @@ class ust_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("pivot", ctypes.c_int32),
                 ("ecc", ctypes.c_int32), ("trees", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("draws", ctypes.c_int64), ("pop_rounds", ctypes.c_int64),
-                ("max_pop_rounds", ctypes.c_int32), ("max_tree_depth", ctypes.c_int32),
+                ("max_pop_rounds", ctypes.c_int32), ("max_round_pops", ctypes.c_int32),
                 ("farness", ctypes.c_int64), ("cg_iters", ctypes.c_int32),
                 ("cg_refinements", ctypes.c_int32), ("cg_relres", ctypes.c_double),
                 ("sample_ctas", ctypes.c_int32), ("sample_threads", ctypes.c_int32),

@@ -81,7 +81,7 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     c->delta = op.delta > 0 ? op.delta : 1.0 / (double)n;
     c->kappa = op.kappa > 0 ? op.kappa : 0.3;
     c->cg_tol = op.cg_tol > 0 ? op.cg_tol : 1e-9;
-    c->max_pop_rounds = op.max_pop_rounds > 0 ? op.max_pop_rounds : (int)std::min<int64_t>(4ll * n + 64, 1 << 30);
+    c->max_pop_rounds = op.max_pop_rounds;  // 0: derived from the graph at each launch
     c->max_cg_iters = op.max_cg_iters > 0 ? op.max_cg_iters : 20000;
     c->graph_id = op.graph_id;
     c->stream = reinterpret_cast<cudaStream_t>(op.stream);
@@ -318,7 +318,7 @@ int ust_get_info(const ust_ctx *h, ust_info *out)
     out->draws = c->draws;
     out->pop_rounds = c->pop_rounds;
     out->max_pop_rounds = c->max_rounds_seen;
-    out->max_tree_depth = c->max_depth_seen;
+    out->max_round_pops = c->max_depth_seen;
     out->farness = c->farness;
     out->cg_iters = c->cg_iters;
     out->cg_refinements = c->cg_refinements;

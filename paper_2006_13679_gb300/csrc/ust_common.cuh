@@ -27,8 +27,9 @@ enum : int {
 };
 
 // Per-CTA scratch of the sampling kernel: `kWsArrays` int32 arrays of
-// `stride` entries each, laid out array-major inside one CTA slot.
-constexpr int kWsArrays = 11;
+// `stride` entries each, laid out array-major inside one CTA slot (the last
+// two form one 64-bit array).
+constexpr int kWsArrays = 13;
 
 struct Ctx {
     int n = 0;

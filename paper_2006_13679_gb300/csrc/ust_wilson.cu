@@ -7,20 +7,27 @@
 //
 //  1. Cycle popping (Wilson's cycle-popping theorem, used in Appendix A.2).
 //     Every vertex v != u has a stack of random neighbours, entry k being the
-//     Philox draw keyed by (v, k, tree, graph). The current stack tops form a
-//     functional graph. Each round classifies every unresolved vertex by
-//     pointer jumping with a min-label: a vertex whose path reaches the
-//     resolved set (vertices already known to reach u) is resolved and gets
-//     its depth in T; every other vertex ends in a cycle, and the smallest
-//     vertex of each cycle walks it once and pops it (every vertex on it
-//     advances to its next stack entry). All disjoint cycles are popped in
-//     the same round; by the theorem the final tree does not depend on that
-//     order, so it equals the loop-erased-walk tree with the same stacks.
-//  2. DFS intervals of T (Algorithm 2's discovery/finish times): vertices are
-//     bucketed by depth, subtree sizes are accumulated bottom-up level by
-//     level, children receive offsets from an atomic cursor of their parent
-//     and preorder positions are assigned top-down. Any child order gives
-//     valid nested intervals, and the subtree test does not depend on it.
+//     Philox draw keyed by (v, k, tree, graph); the stack tops form a
+//     functional graph whose sink is u. Popping every cycle until none is
+//     left gives the same tree as the loop-erased walks, whatever the order.
+//     - Round 0: the cycle vertices of the first functional graph are what
+//       in-degree peeling leaves behind. Peeling is asynchronous: a vertex
+//       whose in-degree drops to zero is continued by the thread that removed
+//       its last in-edge, so it costs O(n) atomics and no barriers.
+//     - Later rounds: every new cycle passes through a vertex redrawn in the
+//       previous round. Each redrawn vertex x walks the stack tops until the
+//       next redrawn vertex S(x) or a vertex known to reach u. Cycles of the
+//       small graph x -> S(x) are found by min-label pointer jumping; their
+//       segments are the vertex cycles, which are popped (every vertex on
+//       them advances to its next stack entry). Segments that reach u are
+//       marked, so later walks stop there.
+//  2. DFS intervals of T (Algorithm 2's discovery/finish times), without
+//     level barriers: subtree sizes by a packed 64-bit "pending children |
+//     size" counter where the last arriving child carries the sum upwards;
+//     child offsets from an atomic cursor of the parent; preorder numbers by
+//     ancestor walks that stop at the first numbered ancestor and write the
+//     path back. Any child order gives valid nested intervals and the
+//     subtree test does not depend on it.
 //  3. Algorithm 2 with the inclusive subtree test: thread v walks P(v) up
 //     B_u and adds +1 / -1 for every BFS edge that T uses downwards /
 //     upwards above v. Counts go to the CTA's partial row Rp; a second kernel
@@ -63,7 +70,7 @@ struct SampleParams {
     int32_t *Rp;
     long long t_begin, t_end;
     unsigned long long *next_tree;
-    unsigned long long *stats;  // [0] draws, [1] rounds, [2] max rounds, [3] max depth
+    unsigned long long *stats;  // [0] draws, [1] rounds, [2] max rounds, [3] max pops in one round
     int *status;
     int max_rounds, max_steps;
     int mode;  // 0: aggregate, 1: export trees
@@ -80,64 +87,33 @@ __device__ __forceinline__ int stack_entry(const SampleParams &p, int v, uint32_
     return __ldg(p.ci + b + (int)idx);
 }
 
-// In-place exclusive prefix sum of a[0..len) by one CTA.
-template <int BT>
-__device__ void block_exclusive_scan(int32_t *a, int len, int *s_warp)
-{
-    constexpr int W = BT / 32;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int carry = 0;
-    for (int base = 0; base < len; base += BT) {
-        const int i = base + threadIdx.x;
-        const int x = (i < len) ? a[i] : 0;
-        int incl = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_warp[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            int w = (lane < W) ? s_warp[lane] : 0;
-            int wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            if (lane < W) s_warp[lane] = wi - w;  // exclusive warp offsets
-            if (lane == 31) s_warp[W] = wi;       // chunk total
-        }
-        __syncthreads();
-        if (i < len) a[i] = carry + s_warp[wid] + incl - x;
-        carry += s_warp[W];
-        __syncthreads();
-    }
-}
+constexpr int kFinal = -1;  // mark of vertices known to reach u
 
 template <int BT>
 __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 {
     const int n = p.n, u = p.u, tid = threadIdx.x;
-    int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * p.stride;
-    int32_t *nxt = base;
-    int32_t *pop = base + 1 * p.stride;
-    int32_t *tdep = base + 2 * p.stride;
-    int32_t *actA = base + 3 * p.stride;
-    int32_t *actB = base + 4 * p.stride;
-    int32_t *J0 = base + 5 * p.stride, *J1 = base + 6 * p.stride;
-    int32_t *L0 = base + 7 * p.stride, *L1 = base + 8 * p.stride;
-    int32_t *D0 = base + 9 * p.stride, *D1 = base + 10 * p.stride;
+    const long long S_ = p.stride;
+    int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
+    int32_t *nxt = base;              // stack tops; the tree's parent array at the end
+    int32_t *pop = base + 1 * S_;     // stack depth of the current top
+    int32_t *mark = base + 2 * S_;    // in-degree (round 0), then kFinal / round stamp
+    int32_t *pos = base + 3 * S_;     // index of a redrawn vertex in the round's list
+    int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // redrawn vertices of this / next round
+    int32_t *Sx = base + 6 * S_;      // S(x) as an index into the round's list, -1 = reaches u
+    int32_t *J0 = base + 7 * S_, *J1 = base + 8 * S_;
+    int32_t *L0 = base + 9 * S_, *L1 = base + 10 * S_;
+    unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);  // 2 arrays
     int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_maxdepth;
+    __shared__ int s_cnt, s_err;
     __shared__ unsigned long long s_draws;
     __shared__ int s_warp[BT / 32 + 1];
 
     unsigned long long my_draws = 0, my_rounds = 0;
-    int my_max_rounds = 0, my_max_depth = 0;
+    int my_max_rounds = 0, my_max_pops = 0;
+    (void)s_warp;
 
     for (;;) {
         if (tid == 0) s_tree = p.t_begin + (long long)atomicAdd(p.next_tree, 1ull);
@@ -149,70 +125,103 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         // ---- 1. cycle popping --------------------------------------------
         for (int v = tid; v < n; v += BT) {
             pop[v] = 0;
-            if (v == u) {
-                nxt[v] = -1;
-                tdep[v] = 0;
-            } else {
-                nxt[v] = stack_entry(p, v, 0u, tree);
-                tdep[v] = -1;
-            }
-            if (v < n - 1) actA[v] = (v < u) ? v : v + 1;
+            mark[v] = 0;
+            nxt[v] = (v == u) ? -1 : stack_entry(p, v, 0u, tree);
         }
         if (tid == 0) {
             s_draws = (unsigned long long)(n - 1);
-            s_maxdepth = 0;
             s_cnt = 0;
+            s_err = 0;
         }
         __syncthreads();
+        // round 0: in-degrees of the first functional graph
+        for (int v = tid; v < n; v += BT)
+            if (v != u) atomicAdd(&mark[nxt[v]], 1);
+        __syncthreads();
+        for (int v = tid; v < n; v += BT)
+            if (v != u && mark[v] == 0) mark[v] = -1;  // initial leaves
+        __syncthreads();
+        for (int v = tid; v < n; v += BT) {
+            if (v == u || mark[v] != -1) continue;
+            int x = v;
+            for (int guard = 0; guard < n; ++guard) {
+                const int y = nxt[x];
+                if (y == u || atomicSub(&mark[y], 1) != 1) break;
+                x = y;  // this thread removed y's last in-edge: peel y next
+            }
+        }
+        __syncthreads();
+        for (int v = tid; v < n; v += BT)
+            if (v != u && mark[v] > 0) XA[atomicAdd(&s_cnt, 1)] = v;  // cycle vertices
+        __syncthreads();
+        int nX = s_cnt;
+        for (int v = tid; v < n; v += BT) mark[v] = (v == u) ? kFinal : 0;
+        __syncthreads();
 
-        int nact = n - 1, rounds = 0, tree_depth = 0;
-        int32_t *act = actA, *act_next = actB;
+        int rounds = 0;
         bool failed = false;
-        while (nact > 0) {
-            if (++rounds > p.max_rounds) {
+        int32_t *X = XA, *Xn = XB;
+        while (nX > 0) {
+            ++rounds;
+            if (rounds > p.max_rounds) {
                 failed = true;
                 if (tid == 0) atomicOr(p.status, kStatusPopRounds);
                 break;
             }
-            for (int i = tid; i < nact; i += BT) {
-                const int v = act[i];
-                J0[v] = nxt[v];
-                L0[v] = v;
-                D0[v] = 1;
+            if (tid == 0) {
+                s_draws += (unsigned long long)nX;
+                s_cnt = 0;
+                my_max_pops = max(my_max_pops, nX);
+            }
+            // (a) pop: every vertex on a cycle advances to its next stack entry
+            for (int i = tid; i < nX; i += BT) {
+                const int x = X[i];
+                const int k = pop[x] + 1;
+                pop[x] = k;
+                nxt[x] = stack_entry(p, x, (uint32_t)k, tree);
+                mark[x] = rounds;
+                pos[x] = i;
             }
             __syncthreads();
-            // Synchronous pointer jumping. Label L[v] = min vertex id on the
-            // path from v up to (not including) J[v]; resolved vertices are
-            // absorbing and carry label -1. When a step changes nothing, L[v]
-            // is the minimum over everything reachable from v.
-            int32_t *Jc = J0, *Lc = L0, *Dc = D0, *Jn = J1, *Ln = L1, *Dn = D1;
+            // (b) S(x): first redrawn vertex or known-final vertex after x
+            for (int i = tid; i < nX; i += BT) {
+                int y = nxt[X[i]];
+                int res = -2;
+                for (int guard = 0; guard <= n; ++guard) {
+                    const int m = mark[y];
+                    if (m == kFinal) { res = -1; break; }
+                    if (m == rounds) { res = pos[y]; break; }
+                    y = nxt[y];
+                }
+                if (res == -2) { s_err = 1; res = -1; }
+                Sx[i] = res;
+                J0[i] = res;
+                L0[i] = (res < 0) ? -1 : i;
+            }
+            __syncthreads();
+            // (c) min-label pointer jumping on the graph i -> S(i); -1 absorbs
+            int32_t *Jc = J0, *Lc = L0, *Jn = J1, *Ln = L1;
             bool converged = false;
             for (int step = 0; step < p.max_steps; ++step) {
                 int changed = 0;
-                for (int i = tid; i < nact; i += BT) {
-                    const int v = act[i];
-                    const int j = Jc[v];
-                    const int lv = Lc[v];
-                    const int dv = Dc[v];
-                    int nj, nl, nd;
-                    if (tdep[j] >= 0) {
-                        nj = j;
+                for (int i = tid; i < nX; i += BT) {
+                    const int j = Jc[i];
+                    const int li = Lc[i];
+                    int nj, nl;
+                    if (j < 0) {
+                        nj = -1;
                         nl = -1;
-                        nd = dv;
                     } else {
                         nj = Jc[j];
-                        nl = min(lv, Lc[j]);
-                        nd = dv + Dc[j];
+                        nl = min(li, Lc[j]);
                     }
-                    Jn[v] = nj;
-                    Ln[v] = nl;
-                    Dn[v] = nd;
-                    changed |= (nl != lv) || (nl == -1 && tdep[nj] < 0);
+                    Jn[i] = nj;
+                    Ln[i] = nl;
+                    changed |= (nl != li);
                 }
                 int32_t *tmp;
                 tmp = Jc; Jc = Jn; Jn = tmp;
                 tmp = Lc; Lc = Ln; Ln = tmp;
-                tmp = Dc; Dc = Dn; Dn = tmp;
                 if (!__syncthreads_or(changed)) {
                     converged = true;
                     break;
@@ -223,47 +232,55 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
                 break;
             }
-            // Classify: resolve, or keep and pop the cycle whose minimum is v.
-            for (int i = tid; i < nact; i += BT) {
-                const int v = act[i];
-                const int lv = Lc[v];
-                if (lv == -1) {
-                    const int d = Dc[v] + tdep[Jc[v]];
-                    tdep[v] = d;
-                    tree_depth = max(tree_depth, d);
-                } else {
-                    act_next[atomicAdd(&s_cnt, 1)] = v;
-                    if (lv == v) {
-                        int x = nxt[v], len = 1;
-                        while (x != v && Lc[x] == v && len <= nact) {
-                            x = nxt[x];
-                            ++len;
-                        }
-                        if (x == v) {
-                            int y = v;
-                            do {
-                                const int z = nxt[y];
-                                const int k = pop[y] + 1;
-                                pop[y] = k;
-                                nxt[y] = stack_entry(p, y, (uint32_t)k, tree);
-                                y = z;
-                            } while (y != v);
-                            atomicAdd(&s_draws, (unsigned long long)len);
-                        }
+            // (d) segments that reach u become final; the smallest node of
+            //     each cycle of i -> S(i) flags the cycle (pos[x] = -1)
+            for (int i = tid; i < nX; i += BT) {
+                const int li = Lc[i];
+                if (li == -1) {
+                    int y = X[i];
+                    for (int guard = 0; guard <= n; ++guard) {
+                        mark[y] = kFinal;
+                        y = nxt[y];
+                        const int m = mark[y];
+                        if (m == kFinal || m == rounds) break;
+                    }
+                } else if (li == i) {
+                    int j = Sx[i], len = 1;
+                    while (j != i && j >= 0 && Lc[j] == i && len <= nX) {
+                        j = Sx[j];
+                        ++len;
+                    }
+                    if (j == i) {
+                        j = i;
+                        do {
+                            pos[X[j]] = -1;
+                            j = Sx[j];
+                        } while (j != i);
                     }
                 }
             }
             __syncthreads();
-            nact = s_cnt;
-            int32_t *tmp = act; act = act_next; act_next = tmp;
+            // (e) the vertex cycles: each flagged x with its segment up to S(x)
+            for (int i = tid; i < nX; i += BT) {
+                int y = X[i];
+                if (pos[y] != -1) continue;
+                for (int guard = 0; guard <= n; ++guard) {
+                    Xn[atomicAdd(&s_cnt, 1)] = y;
+                    y = nxt[y];
+                    if (mark[y] == rounds) break;
+                }
+            }
             __syncthreads();
-            if (tid == 0) s_cnt = 0;
+            nX = s_cnt;
+            int32_t *tmp = X; X = Xn; Xn = tmp;
+            if (s_err) {
+                failed = true;
+                if (tid == 0) atomicOr(p.status, kStatusBadState);
+                break;
+            }
             __syncthreads();
         }
         if (failed) break;
-
-        atomicMax(&s_maxdepth, tree_depth);
-        my_max_depth = max(my_max_depth, tree_depth);
         if (tid == 0) {
             my_draws += s_draws;
             my_rounds += (unsigned long long)rounds;
@@ -279,46 +296,60 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             __syncthreads();
             continue;
         }
-        __syncthreads();
 
         // ---- 2. DFS intervals ---------------------------------------------
-        const int dmax = s_maxdepth;
-        int32_t *lvl = J0, *fill = J1, *ord = actA;
-        int32_t *sz = L0, *cur = L1, *off = D0, *pre = D1;
-        for (int d = tid; d <= dmax + 1; d += BT) lvl[d] = 0;
+        int32_t *cur = mark, *off = pos, *pre = XA;
         for (int v = tid; v < n; v += BT) {
-            sz[v] = 1;
+            P[v] = 0ull;
             cur[v] = 0;
+            pre[v] = (v == u) ? 0 : -1;
         }
         __syncthreads();
-        for (int v = tid; v < n; v += BT) atomicAdd(&lvl[tdep[v]], 1);
+        for (int v = tid; v < n; v += BT)
+            if (v != u) atomicAdd(&P[nxt[v]], 1ull << 32);  // pending children
         __syncthreads();
-        block_exclusive_scan<BT>(lvl, dmax + 2, s_warp);
-        for (int d = tid; d <= dmax + 1; d += BT) fill[d] = lvl[d];
-        __syncthreads();
-        for (int v = tid; v < n; v += BT) ord[atomicAdd(&fill[tdep[v]], 1)] = v;
-        __syncthreads();
-        for (int d = dmax; d >= 1; --d) {
-            const int s = lvl[d], e = lvl[d + 1];
-            for (int i = s + tid; i < e; i += BT) {
-                const int v = ord[i];
-                atomicAdd(&sz[nxt[v]], sz[v]);
-            }
-            __syncthreads();
-        }
+        // subtree sizes: high word = children not yet finished, low word =
+        // sum of finished children's sizes; the last child continues upwards
         for (int v = tid; v < n; v += BT) {
-            if (v != u) off[v] = 1 + atomicAdd(&cur[nxt[v]], sz[v]);
-        }
-        if (tid == 0) pre[u] = 0;
-        __syncthreads();
-        for (int d = 1; d <= dmax; ++d) {
-            const int s = lvl[d], e = lvl[d + 1];
-            for (int i = s + tid; i < e; i += BT) {
-                const int v = ord[i];
-                pre[v] = pre[nxt[v]] + off[v];
+            if (v == u || (P[v] >> 32) != 0ull) continue;
+            unsigned long long carry = 1ull;
+            int x = v;
+            for (int guard = 0; guard < n; ++guard) {
+                const int par = nxt[x];
+                if (par < 0) break;
+                const unsigned long long old = atomicAdd(&P[par], carry - (1ull << 32));
+                if ((old >> 32) != 1ull) break;
+                carry = (old & 0xFFFFFFFFull) + carry + 1ull;
+                x = par;
             }
-            __syncthreads();
         }
+        __syncthreads();
+        // offsets of children inside their parent's interval
+        for (int v = tid; v < n; v += BT) {
+            if (v == u) continue;
+            const int sz = (int)(P[v] & 0xFFFFFFFFull) + 1;
+            off[v] = 1 + atomicAdd(&cur[nxt[v]], sz);
+        }
+        __syncthreads();
+        // preorder numbers: walk up to the first numbered ancestor, write back
+        for (int v = tid; v < n; v += BT) {
+            if (pre[v] >= 0) continue;
+            int acc = 0, x = v, px = -1;
+            for (int guard = 0; guard < n; ++guard) {
+                px = pre[x];
+                if (px >= 0) break;
+                acc += off[x];
+                x = nxt[x];
+            }
+            const int total = px + acc;
+            int y = v, s = 0;
+            while (y != x) {
+                pre[y] = total - s;
+                s += off[y];
+                y = nxt[y];
+            }
+        }
+        __syncthreads();
 
         // ---- 3. Algorithm 2 ------------------------------------------------
         for (int v = tid; v < n; v += BT) {
@@ -330,10 +361,12 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 const int a = __ldg(p.bpar + b);
                 if (nxt[b] == a) {
                     const int lo = pre[b];
-                    cnt += (lo <= pv && pv < lo + sz[b]) ? 1 : 0;
+                    const int sz = (int)(P[b] & 0xFFFFFFFFull) + 1;
+                    cnt += (lo <= pv && pv < lo + sz) ? 1 : 0;
                 } else if (nxt[a] == b) {
                     const int lo = pre[a];
-                    cnt -= (lo <= pv && pv < lo + sz[a]) ? 1 : 0;
+                    const int sz = (int)(P[a] & 0xFFFFFFFFull) + 1;
+                    cnt -= (lo <= pv && pv < lo + sz) ? 1 : 0;
                 }
                 b = a;
             }
@@ -346,8 +379,8 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         atomicAdd(p.stats + 0, my_draws);
         atomicAdd(p.stats + 1, my_rounds);
         atomicMax(p.stats + 2, (unsigned long long)my_max_rounds);
+        atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
     }
-    atomicMax(p.stats + 3, (unsigned long long)my_max_depth);
 }
 
 // out[v] += sum over partial rows of Rp[c][v] (exact, fixed order).
@@ -412,7 +445,13 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     p.next_tree = st + 4;
     p.stats = st;
     p.status = reinterpret_cast<int *>(st + 5);
-    p.max_rounds = c->max_pop_rounds;
+    // Every round pops at least one cycle and the expected number of pops per
+    // tree is below sum_v deg(v) r(u, v) <= 2m ecc(u) (Lemma in Appendix A.2),
+    // so the default bound is far above anything a correct run reaches.
+    p.max_rounds = c->max_pop_rounds > 0
+                       ? c->max_pop_rounds
+                       : (int)std::min<int64_t>(16ll * ((int64_t)c->nnz * std::max(1, c->ecc) + c->n) + 1024,
+                                                1ll << 30);
     int lg = 0;
     while ((1ll << lg) < (long long)c->n) ++lg;
     p.max_steps = lg + 4;
