@@ -121,6 +121,9 @@ typedef struct {
     double combine_ms;      /* the diagonal combination */
     int64_t last_trees;     /* trees processed by the last sampling launch */
     int64_t last_draws;     /* stack entries drawn by the last sampling launch */
+    /* SM clock cycles spent by the last sampling launch in its three phases,
+     * summed over trees: cycle popping, DFS intervals, Algorithm 2 */
+    int64_t last_phase_cycles[3];
 } ust_info;
 
 /* Fills *o with the defaults. */

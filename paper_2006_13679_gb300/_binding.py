@@ -46,10 +46,15 @@ class ust_info(ctypes.Structure):
                 ("sample_ctas", ctypes.c_int32), ("sample_threads", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("bfs_ms", ctypes.c_double), ("sample_ms", ctypes.c_double),
                 ("reduce_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("combine_ms", ctypes.c_double),
-                ("last_trees", ctypes.c_int64), ("last_draws", ctypes.c_int64)]
+                ("last_trees", ctypes.c_int64), ("last_draws", ctypes.c_int64),
+                ("last_phase_cycles", ctypes.c_int64 * 3)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "_length_") else v
+        return out
 
 
 # name -> (restype, argtypes)

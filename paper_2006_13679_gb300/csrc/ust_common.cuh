@@ -68,6 +68,8 @@ struct Ctx {
     double *d_x = nullptr;      // column L^+[:, u]
     bool x_valid = false;
     int solve_blocks = 0;
+    int32_t *d_heavy = nullptr;  // rows summed by a whole CTA in the SpMVs
+    int n_heavy = 0;
 
     // phase timers: event pairs for bfs, sample kernel, reduce, solve, combine
     enum { kEvBfs = 0, kEvSample = 1, kEvReduce = 2, kEvSolve = 3, kEvCombine = 4, kEvPhases = 5 };
@@ -75,6 +77,7 @@ struct Ctx {
     bool ev_used[kEvPhases] = {};
     int64_t launches = 0;
     int64_t last_trees = 0, last_draws = 0;
+    int64_t last_phase_cycles[3] = {0, 0, 0};
 
     // committed state
     int64_t trees = 0;

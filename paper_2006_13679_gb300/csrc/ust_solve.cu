@@ -37,17 +37,19 @@ __device__ __forceinline__ double warp_sum_partials(const double *part, int coun
     return s;
 }
 
-// Block-wide sum of one double per thread, result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double *s_tmp)
+// Block-wide sum of one value per thread (fixed shuffle tree), result valid
+// in thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *s_tmp)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) s_tmp[wid] = v;
     __syncthreads();
-    double r = 0.0;
+    T r = T(0);
     if (wid == 0) {
-        r = (lane < kSolveThreads / 32) ? s_tmp[lane] : 0.0;
+        r = (lane < kSolveThreads / 32) ? s_tmp[lane] : T(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
     }
@@ -55,29 +57,51 @@ __device__ __forceinline__ double block_sum(double v, double *s_tmp)
     return r;
 }
 
+// Rows with more than kHeavyRow arcs are summed by a whole CTA each (the
+// first `nh` blocks of an SpMV launch); the other blocks give every light row
+// a group of kRowGroup lanes. Both reductions use a fixed order.
+constexpr int kHeavyRow = 256;
+
 // r64 = b - L x64; partials of sum(r) and sum(r^2).
 __global__ void __launch_bounds__(kSolveThreads) residual_f64_kernel(int n, int u, const int32_t *__restrict__ rp,
                                                                      const int32_t *__restrict__ ci,
+                                                                     const int32_t *__restrict__ heavy, int nh,
                                                                      const double *__restrict__ x,
                                                                      double *__restrict__ r, double *part)
 {
     __shared__ double s_tmp[kSolveThreads / 32];
+    const double inv_n = 1.0 / (double)n;
+    if ((int)blockIdx.x < nh) {
+        const int v = heavy[blockIdx.x];
+        const int e0 = __ldg(rp + v), e1 = __ldg(rp + v + 1);
+        double s = 0.0;
+        for (int e = e0 + threadIdx.x; e < e1; e += kSolveThreads) s += x[__ldg(ci + e)];
+        s = block_sum(s, s_tmp);
+        if (threadIdx.x == 0) {
+            const double rv = ((v == u ? 1.0 : 0.0) - inv_n) - ((double)(e1 - e0) * x[v] - s);
+            r[v] = rv;
+            part[blockIdx.x * 2 + 0] = rv;
+            part[blockIdx.x * 2 + 1] = rv * rv;
+        }
+        return;
+    }
     const int g = threadIdx.x % kRowGroup;
     const int rows_per_block = kSolveThreads / kRowGroup;
-    const double inv_n = 1.0 / (double)n;
+    const int lb = blockIdx.x - nh, lgrid = gridDim.x - nh;
     double sr = 0.0, srr = 0.0;
-    for (int v0 = blockIdx.x * rows_per_block; v0 < n; v0 += gridDim.x * rows_per_block) {
+    for (int v0 = lb * rows_per_block; v0 < n; v0 += lgrid * rows_per_block) {
         const int v = v0 + threadIdx.x / kRowGroup;
         double s = 0.0;
         int e0 = 0, e1 = 0;
         if (v < n) {
             e0 = __ldg(rp + v);
             e1 = __ldg(rp + v + 1);
+            if (e1 - e0 > kHeavyRow) e1 = e0;  // summed by a heavy-row block
             for (int e = e0 + g; e < e1; e += kRowGroup) s += x[__ldg(ci + e)];
         }
 #pragma unroll
         for (int o = kRowGroup / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, kRowGroup);
-        if (v < n && g == 0) {
+        if (v < n && g == 0 && e1 > e0) {
             const double lx = (double)(e1 - e0) * x[v] - s;
             const double bv = (v == u ? 1.0 : 0.0) - inv_n;
             const double rv = bv - lx;
@@ -128,25 +152,43 @@ __global__ void __launch_bounds__(kSolveThreads) inner_start_kernel(int n, int n
 // q = L p (FP32); partials of p.q.
 __global__ void __launch_bounds__(kSolveThreads) spmv_f32_kernel(int n, const int32_t *__restrict__ rp,
                                                                  const int32_t *__restrict__ ci,
+                                                                 const int32_t *__restrict__ heavy, int nh,
                                                                  const float *__restrict__ p, float *__restrict__ q,
                                                                  double *part_out)
 {
     __shared__ double s_tmp[kSolveThreads / 32];
+    __shared__ float s_tmpf[kSolveThreads / 32];
+    if ((int)blockIdx.x < nh) {
+        const int v = heavy[blockIdx.x];
+        const int e0 = __ldg(rp + v), e1 = __ldg(rp + v + 1);
+        float s = 0.0f;
+        for (int e = e0 + threadIdx.x; e < e1; e += kSolveThreads) s += p[__ldg(ci + e)];
+        s = block_sum(s, s_tmpf);
+        if (threadIdx.x == 0) {
+            const float pv = p[v];
+            const float qv = (float)(e1 - e0) * pv - s;
+            q[v] = qv;
+            part_out[blockIdx.x] = (double)pv * (double)qv;
+        }
+        return;
+    }
     const int g = threadIdx.x % kRowGroup;
     const int rows_per_block = kSolveThreads / kRowGroup;
+    const int lb = blockIdx.x - nh, lgrid = gridDim.x - nh;
     double pq = 0.0;
-    for (int v0 = blockIdx.x * rows_per_block; v0 < n; v0 += gridDim.x * rows_per_block) {
+    for (int v0 = lb * rows_per_block; v0 < n; v0 += lgrid * rows_per_block) {
         const int v = v0 + threadIdx.x / kRowGroup;
         float s = 0.0f;
         int e0 = 0, e1 = 0;
         if (v < n) {
             e0 = __ldg(rp + v);
             e1 = __ldg(rp + v + 1);
+            if (e1 - e0 > kHeavyRow) e1 = e0;
             for (int e = e0 + g; e < e1; e += kRowGroup) s += p[__ldg(ci + e)];
         }
 #pragma unroll
         for (int o = kRowGroup / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, kRowGroup);
-        if (v < n && g == 0) {
+        if (v < n && g == 0 && e1 > e0) {
             const float pv = p[v];
             const float qv = (float)(e1 - e0) * pv - s;
             q[v] = qv;
@@ -270,27 +312,39 @@ int alloc_solver(Ctx *c)
 {
     const size_t n = (size_t)c->n;
     c->solve_blocks = std::max(1, std::min<int>(c->num_sms * 2, (int)((n + kSolveThreads - 1) / kSolveThreads)));
+    // rows summed by a whole CTA in the SpMVs
+    std::vector<int32_t> rp(n + 1), heavy;
+    UST_CUDA_TRY(cudaMemcpyAsync(rp.data(), c->d_rp, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t v = 0; v < n; ++v)
+        if (rp[v + 1] - rp[v] > kHeavyRow) heavy.push_back((int32_t)v);
+    c->n_heavy = (int)heavy.size();
+    if (cudaMalloc(&c->d_heavy, std::max<size_t>(1, heavy.size()) * sizeof(int32_t)) != cudaSuccess)
+        return fail(c, UST_ENOMEM, "heavy rows");
+    if (!heavy.empty())
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_heavy, heavy.data(), heavy.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, c->stream));
+    const size_t parts = 8 * ((size_t)c->solve_blocks + (size_t)c->n_heavy) + 8;
     if (cudaMalloc(&c->d_f32, 5 * n * sizeof(float)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver FP32 vectors");
     if (cudaMalloc(&c->d_f64, 2 * n * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver FP64 vectors");
     if (cudaMalloc(&c->d_x, n * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "column");
-    // partials: 4 areas of 2*blocks doubles + 2 scalars
-    if (cudaMalloc(&c->d_red, (8 * (size_t)c->solve_blocks + 8) * sizeof(double)) != cudaSuccess)
-        return fail(c, UST_ENOMEM, "solver partials");
-    if (cudaMallocHost(&c->h_red, (8 * (size_t)c->solve_blocks + 8) * sizeof(double)) != cudaSuccess)
+    if (cudaMalloc(&c->d_red, parts * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver partials");
+    if (cudaMallocHost(&c->h_red, parts * sizeof(double)) != cudaSuccess)
         return fail(c, UST_ENOMEM, "pinned solver partials");
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return UST_OK;
 }
 
 int run_solve(Ctx *c)
 {
-    const int n = c->n, nb = c->solve_blocks, T = kSolveThreads;
+    const int n = c->n, nb = c->solve_blocks, nh = c->n_heavy, ns = nb + nh, T = kSolveThreads;
     cudaStream_t st = c->stream;
     float *r = c->d_f32, *z = r + n, *p = z + n, *q = p + n, *d = q + n;
     double *x = c->d_x, *r64 = c->d_f64;
-    double *part_res = c->d_red;              // 2*nb
-    double *part_a = part_res + 2 * nb;       // 2*nb
-    double *part_b = part_a + 2 * nb;         // 2*nb
-    double *sc = part_b + 2 * nb;             // 2 scalars
+    double *part_res = c->d_red;              // 2*ns
+    double *part_a = part_res + 2 * ns;       // 2*ns
+    double *part_b = part_a + 2 * ns;         // 2*ns
+    double *sc = part_b + 2 * ns;             // 2 scalars
     phase_begin(c, Ctx::kEvSolve);
     UST_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), st));
 
@@ -300,18 +354,18 @@ int run_solve(Ctx *c)
     int total_inner = 0, refinements = 0;
     double relres = 1.0;
     for (;;) {
-        residual_f64_kernel<<<nb, T, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, x, r64, part_res);
+        residual_f64_kernel<<<ns, T, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
-        UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, st));
         UST_CUDA_TRY(cudaStreamSynchronize(st));
         double rr = 0.0;
-        for (int i = 0; i < nb; ++i) rr += c->h_red[2 * i + 1];
+        for (int i = 0; i < ns; ++i) rr += c->h_red[2 * i + 1];
         relres = sqrt(rr) / bnorm;
         if (relres <= c->cg_tol) break;
         if (refinements >= 30) break;
         ++refinements;
-        inner_start_kernel<<<nb, T, 0, st>>>(n, nb, c->d_rp, r64, part_res, r, z, p, d, part_a);
+        inner_start_kernel<<<nb, T, 0, st>>>(n, ns, c->d_rp, r64, part_res, r, z, p, d, part_a);
         store_rz_kernel<<<1, 32, 0, st>>>(nb, part_a, sc);
         c->launches += 2;
         UST_CUDA_TRY(cudaGetLastError());
@@ -319,14 +373,13 @@ int run_solve(Ctx *c)
         UST_CUDA_TRY(cudaStreamSynchronize(st));
         double rz0 = 0.0;
         for (int i = 0; i < nb; ++i) rz0 += c->h_red[i];
-        // ||r||^2 of the inner start, for the inner stopping test
-        double r0 = rr;
+        const double r0 = rr;  // ||r||^2 at the start of the inner solve
         int it = 0, par = 0;
         bool inner_done = (rz0 <= 0.0);
         while (!inner_done && it < c->max_cg_iters) {
             for (int k = 0; k < check_every && it < c->max_cg_iters; ++k, ++it) {
-                spmv_f32_kernel<<<nb, T, 0, st>>>(n, c->d_rp, c->d_ci, p, q, part_a);
-                pcg_update_kernel<<<nb, T, 0, st>>>(n, nb, c->d_rp, part_a, sc, par, d, r, z, p, q, part_b);
+                spmv_f32_kernel<<<ns, T, 0, st>>>(n, c->d_rp, c->d_ci, c->d_heavy, nh, p, q, part_a);
+                pcg_update_kernel<<<nb, T, 0, st>>>(n, ns, c->d_rp, part_a, sc, par, d, r, z, p, q, part_b);
                 pcg_direction_kernel<<<nb, T, 0, st>>>(n, nb, part_b, sc, par, z, p);
                 c->launches += 3;
                 par ^= 1;
@@ -348,13 +401,13 @@ int run_solve(Ctx *c)
     c->launches += 2;
     UST_CUDA_TRY(cudaGetLastError());
     // residual of the projected solution
-    residual_f64_kernel<<<nb, T, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, x, r64, part_res);
+    residual_f64_kernel<<<ns, T, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
     c->launches += 1;
     phase_end(c, Ctx::kEvSolve);
-    UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, st));
     UST_CUDA_TRY(cudaStreamSynchronize(st));
     double rr = 0.0;
-    for (int i = 0; i < nb; ++i) rr += c->h_red[2 * i + 1];
+    for (int i = 0; i < ns; ++i) rr += c->h_red[2 * i + 1];
     relres = sqrt(rr) / bnorm;
     c->cg_iters = total_inner;
     c->cg_refinements = refinements;

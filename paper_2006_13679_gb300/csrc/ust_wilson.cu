@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     __shared__ int s_warp[BT / 32 + 1];
 
     unsigned long long my_draws = 0, my_rounds = 0;
+    unsigned long long cyc_pop = 0, cyc_int = 0, cyc_agg = 0;  // thread 0: clock64 per phase
     int my_max_rounds = 0, my_max_pops = 0;
     (void)s_warp;
 
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         const long long t = s_tree;
         if (t >= p.t_end) break;
         const uint32_t tree = (uint32_t)t;
+        const long long c0 = clock64();
 
         // ---- 1. cycle popping --------------------------------------------
         for (int v = tid; v < n; v += BT) {
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         }
 
         // ---- 2. DFS intervals ---------------------------------------------
+        const long long c1 = clock64();
         int32_t *cur = mark, *off = pos, *pre = XA;
         for (int v = tid; v < n; v += BT) {
             P[v] = 0ull;
@@ -308,10 +311,14 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         for (int v = tid; v < n; v += BT)
             if (v != u) atomicAdd(&P[nxt[v]], 1ull << 32);  // pending children
         __syncthreads();
+        // leaves are fixed before any counter moves: a vertex whose last
+        // child finishes must not be mistaken for a leaf
+        for (int v = tid; v < n; v += BT) off[v] = (v != u && (P[v] >> 32) == 0ull) ? 1 : 0;
+        __syncthreads();
         // subtree sizes: high word = children not yet finished, low word =
         // sum of finished children's sizes; the last child continues upwards
         for (int v = tid; v < n; v += BT) {
-            if (v == u || (P[v] >> 32) != 0ull) continue;
+            if (off[v] != 1) continue;
             unsigned long long carry = 1ull;
             int x = v;
             for (int guard = 0; guard < n; ++guard) {
@@ -352,6 +359,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         __syncthreads();
 
         // ---- 3. Algorithm 2 ------------------------------------------------
+        const long long c2 = clock64();
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
             const int pv = pre[v];
@@ -373,6 +381,12 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             Rp[v] += cnt;
         }
         __syncthreads();
+        if (tid == 0) {
+            const long long c3 = clock64();
+            cyc_pop += (unsigned long long)(c1 - c0);
+            cyc_int += (unsigned long long)(c2 - c1);
+            cyc_agg += (unsigned long long)(c3 - c2);
+        }
     }
 
     if (tid == 0) {
@@ -380,6 +394,9 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         atomicAdd(p.stats + 1, my_rounds);
         atomicMax(p.stats + 2, (unsigned long long)my_max_rounds);
         atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
+        atomicAdd(p.stats + 8, cyc_pop);
+        atomicAdd(p.stats + 9, cyc_int);
+        atomicAdd(p.stats + 10, cyc_agg);
     }
 }
 
@@ -425,7 +442,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     const int grid = (int)std::min<int64_t>(c->ctas, t1 - t0);
     if (mode == 0)
         UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
-    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 8 * sizeof(int64_t), c->stream));
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 16 * sizeof(int64_t), c->stream));
 
     SampleParams p;
     p.n = c->n;
@@ -479,7 +496,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
     }
-    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
     const int status = (int)c->h_stats[5];
     if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
@@ -487,6 +504,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     if (status) return fail(c, UST_ECUDA, "sampler reported an inconsistent state");
     c->last_trees = t1 - t0;
     c->last_draws = c->h_stats[0];
+    for (int k = 0; k < 3; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
     if (draws) *draws = c->h_stats[0];
     if (rounds) *rounds = c->h_stats[1];
     if (max_rounds) *max_rounds = (int)c->h_stats[2];
