@@ -32,6 +32,8 @@ void release(Ctx *c)
     cudaFree(c->d_bpar);
     cudaFree(c->d_dist);
     cudaFree(c->d_flag);
+    cudaFree(c->d_pathptr);
+    cudaFree(c->d_path);
     cudaFree(c->d_ws);
     cudaFree(c->d_Rp);
     cudaFree(c->d_R);
@@ -113,6 +115,7 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     if (cudaMalloc(&c->d_bpar, (size_t)n * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "bfs parent");
     if (cudaMalloc(&c->d_dist, (size_t)n * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "bfs dist");
     if (cudaMalloc(&c->d_flag, 64) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "flag");
+    if (cudaMalloc(&c->d_pathptr, ((size_t)n + 1) * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "paths");
     if (cudaMalloc(&c->d_stats, 16 * sizeof(int64_t)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "stats");
     if (cudaMallocHost(&c->h_stats, 16 * sizeof(int64_t)) != cudaSuccess)
         return ust::fail(c, UST_ENOMEM, "pinned stats");

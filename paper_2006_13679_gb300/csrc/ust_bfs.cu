@@ -56,6 +56,59 @@ __global__ void bfs_sum_kernel(int n, const int32_t *__restrict__ dist, unsigned
     }
 }
 
+// Exclusive prefix sum of dist into ptr[0..n] by one CTA (ptr[n] = total).
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) path_offsets_kernel(int n, const int32_t *__restrict__ dist,
+                                                                    int32_t *__restrict__ ptr)
+{
+    __shared__ int s_warp[kScanThreads / 32 + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int carry = 0;
+    for (int base = 0; base < n; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int x = (i < n) ? dist[i] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int w = s_warp[lane];
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_warp[lane] = wi - w;
+            if (lane == 31) s_warp[32] = wi;
+        }
+        __syncthreads();
+        if (i < n) ptr[i] = carry + s_warp[wid] + incl - x;
+        carry += s_warp[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ptr[n] = carry;
+}
+
+// path[ptr[v] .. ptr[v+1]) = bfs_parent(v), its parent, ..., u
+__global__ void path_fill_kernel(int n, int u, const int32_t *__restrict__ bpar, const int32_t *__restrict__ ptr,
+                                 int32_t *__restrict__ path)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int k = ptr[v];
+        const int end = ptr[v + 1];
+        int x = v;
+        while (x != u && k < end) {
+            x = bpar[x];
+            path[k++] = x;
+        }
+    }
+}
+
 }  // namespace
 
 int run_bfs(Ctx *c)
@@ -92,6 +145,20 @@ int run_bfs(Ctx *c)
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c->h_stats[1] != 0) return fail(c, UST_ENOTCONNECTED, "graph is not connected");
     c->farness = c->h_stats[0];
+    // the BFS paths P(v), flattened: sum_v dist(u, v) = f^c(u) entries
+    if (c->farness > 0x7FFFFFFFll) return fail(c, UST_EINVAL, "f^c(u) exceeds 2^31 path entries");
+    if (c->farness > c->path_cap) {
+        cudaFree(c->d_path);
+        c->d_path = nullptr;
+        c->path_cap = 0;
+        if (cudaMalloc(&c->d_path, (size_t)c->farness * sizeof(int32_t)) != cudaSuccess)
+            return fail(c, UST_ENOMEM, "BFS paths");
+        c->path_cap = c->farness;
+    }
+    path_offsets_kernel<<<1, kScanThreads, 0, c->stream>>>(n, c->d_dist, c->d_pathptr);
+    path_fill_kernel<<<blocks, threads, 0, c->stream>>>(n, c->pivot, c->d_bpar, c->d_pathptr, c->d_path);
+    c->launches += 2;
+    UST_CUDA_TRY(cudaGetLastError());
     return UST_OK;
 }
 

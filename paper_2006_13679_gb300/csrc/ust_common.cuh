@@ -49,6 +49,8 @@ struct Ctx {
     int32_t *d_rp = nullptr, *d_ci = nullptr;
     int32_t *d_bpar = nullptr, *d_dist = nullptr;
     int32_t *d_flag = nullptr;  // BFS level flag and misc small device scalars
+    int32_t *d_pathptr = nullptr, *d_path = nullptr;  // flattened BFS paths P(v)
+    int64_t path_cap = 0;
 
     // sampling
     int block_threads = 0, ctas = 0;

@@ -65,6 +65,7 @@ struct SampleParams {
     int n, u;
     uint32_t graph, key0, key1;
     const int32_t *rp, *ci, *bpar;
+    const int32_t *path, *pathptr;  // ancestors of v on B_u, v's list at [pathptr[v], pathptr[v+1])
     int32_t *ws;
     long long stride;
     int32_t *Rp;
@@ -89,6 +90,10 @@ __device__ __forceinline__ int stack_entry(const SampleParams &p, int v, uint32_
 
 constexpr int kFinal = -1;  // mark of vertices known to reach u
 
+// Independent walks a thread keeps in flight in the walk passes.
+constexpr int kWalks = 4;
+constexpr int kPathChunk = 4;
+
 template <int BT>
 __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 {
@@ -103,18 +108,20 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     int32_t *Sx = base + 6 * S_;      // S(x) as an index into the round's list, -1 = reaches u
     int32_t *J0 = base + 7 * S_, *J1 = base + 8 * S_;
     int32_t *L0 = base + 9 * S_, *L1 = base + 10 * S_;
-    unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);  // 2 arrays
+    // children bookkeeping: high word = children not yet finished (the
+    // children count while sampling), low word = summed subtree sizes
+    unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);
+    int32_t *cur = mark, *pre = pos, *off = XA;  // interval phase reuses these
     int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
+    constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
     __shared__ int s_cnt, s_err;
     __shared__ unsigned long long s_draws;
-    __shared__ int s_warp[BT / 32 + 1];
 
     unsigned long long my_draws = 0, my_rounds = 0;
     unsigned long long cyc_pop = 0, cyc_int = 0, cyc_agg = 0;  // thread 0: clock64 per phase
     int my_max_rounds = 0, my_max_pops = 0;
-    (void)s_warp;
 
     for (;;) {
         if (tid == 0) s_tree = p.t_begin + (long long)atomicAdd(p.next_tree, 1ull);
@@ -128,6 +135,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         for (int v = tid; v < n; v += BT) {
             pop[v] = 0;
             mark[v] = 0;
+            P[v] = 0ull;
             nxt[v] = (v == u) ? -1 : stack_entry(p, v, 0u, tree);
         }
         if (tid == 0) {
@@ -136,29 +144,45 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             s_err = 0;
         }
         __syncthreads();
-        // round 0: in-degrees of the first functional graph
-        for (int v = tid; v < n; v += BT)
-            if (v != u) atomicAdd(&mark[nxt[v]], 1);
-        __syncthreads();
-        for (int v = tid; v < n; v += BT)
-            if (v != u && mark[v] == 0) mark[v] = -1;  // initial leaves
-        __syncthreads();
+        // in-degrees: mark is consumed by peeling, P keeps the children count
         for (int v = tid; v < n; v += BT) {
-            if (v == u || mark[v] != -1) continue;
-            int x = v;
-            for (int guard = 0; guard < n; ++guard) {
-                const int y = nxt[x];
-                if (y == u || atomicSub(&mark[y], 1) != 1) break;
-                x = y;  // this thread removed y's last in-edge: peel y next
+            if (v == u) continue;
+            const int y = nxt[v];
+            atomicAdd(&mark[y], 1);
+            atomicAdd(&P[y], kChild);
+        }
+        __syncthreads();
+        // round 0: peel from the leaves; a thread that removes a vertex's
+        // last in-edge continues with that vertex. What is left are the
+        // vertices on cycles.
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int x[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                x[k] = (v < n && v != u && (P[v] >> 32) == 0ull) ? v : -1;
+            }
+            for (int guard = 0; guard <= n; ++guard) {
+                int y[kWalks], old[kWalks];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) y[k] = (x[k] >= 0) ? nxt[x[k]] : u;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) old[k] = (y[k] != u) ? atomicSub(&mark[y[k]], 1) : 0;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    x[k] = (old[k] == 1) ? y[k] : -1;
+                    any |= (x[k] >= 0);
+                }
+                if (!any) break;
             }
         }
         __syncthreads();
+        if (tid == 0) mark[u] = kFinal;
         for (int v = tid; v < n; v += BT)
             if (v != u && mark[v] > 0) XA[atomicAdd(&s_cnt, 1)] = v;  // cycle vertices
         __syncthreads();
         int nX = s_cnt;
-        for (int v = tid; v < n; v += BT) mark[v] = (v == u) ? kFinal : 0;
-        __syncthreads();
 
         int rounds = 0;
         bool failed = false;
@@ -170,6 +194,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 if (tid == 0) atomicOr(p.status, kStatusPopRounds);
                 break;
             }
+            __syncthreads();
             if (tid == 0) {
                 s_draws += (unsigned long long)nX;
                 s_cnt = 0;
@@ -179,10 +204,14 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             for (int i = tid; i < nX; i += BT) {
                 const int x = X[i];
                 const int k = pop[x] + 1;
+                const int old = nxt[x];
+                const int y = stack_entry(p, x, (uint32_t)k, tree);
                 pop[x] = k;
-                nxt[x] = stack_entry(p, x, (uint32_t)k, tree);
+                nxt[x] = y;
                 mark[x] = rounds;
                 pos[x] = i;
+                atomicAdd(&P[old], 0ull - kChild);
+                atomicAdd(&P[y], kChild);
             }
             __syncthreads();
             // (b) S(x): first redrawn vertex or known-final vertex after x
@@ -280,7 +309,6 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 if (tid == 0) atomicOr(p.status, kStatusBadState);
                 break;
             }
-            __syncthreads();
         }
         if (failed) break;
         if (tid == 0) {
@@ -290,93 +318,165 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         }
 
         if (p.mode == 1) {
-            const long long off = (t - p.t_begin) * (long long)n;
+            const long long o = (t - p.t_begin) * (long long)n;
             for (int v = tid; v < n; v += BT) {
-                p.next_out[off + v] = nxt[v];
-                if (p.pops_out) p.pops_out[off + v] = pop[v];
+                p.next_out[o + v] = nxt[v];
+                if (p.pops_out) p.pops_out[o + v] = pop[v];
             }
             __syncthreads();
             continue;
         }
+        __syncthreads();
 
         // ---- 2. DFS intervals ---------------------------------------------
         const long long c1 = clock64();
-        int32_t *cur = mark, *off = pos, *pre = XA;
-        for (int v = tid; v < n; v += BT) {
-            P[v] = 0ull;
-            cur[v] = 0;
-            pre[v] = (v == u) ? 0 : -1;
-        }
-        __syncthreads();
-        for (int v = tid; v < n; v += BT)
-            if (v != u) atomicAdd(&P[nxt[v]], 1ull << 32);  // pending children
-        __syncthreads();
-        // leaves are fixed before any counter moves: a vertex whose last
-        // child finishes must not be mistaken for a leaf
-        for (int v = tid; v < n; v += BT) off[v] = (v != u && (P[v] >> 32) == 0ull) ? 1 : 0;
-        __syncthreads();
-        // subtree sizes: high word = children not yet finished, low word =
-        // sum of finished children's sizes; the last child continues upwards
-        for (int v = tid; v < n; v += BT) {
-            if (off[v] != 1) continue;
-            unsigned long long carry = 1ull;
-            int x = v;
-            for (int guard = 0; guard < n; ++guard) {
-                const int par = nxt[x];
-                if (par < 0) break;
-                const unsigned long long old = atomicAdd(&P[par], carry - (1ull << 32));
-                if ((old >> 32) != 1ull) break;
-                carry = (old & 0xFFFFFFFFull) + carry + 1ull;
-                x = par;
+        // Subtree sizes from the leaves (P[v] == 0 exactly for leaves: an
+        // inner vertex always has pending children or a nonzero size sum).
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int x[kWalks];
+            unsigned long long carry[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                if (v < n) {
+                    cur[v] = 0;
+                    pre[v] = (v == u) ? 0 : -1;
+                }
+                x[k] = (v < n && v != u && P[v] == 0ull) ? v : -1;
+                carry[k] = 1ull;
+            }
+            for (int guard = 0; guard <= n; ++guard) {
+                int par[kWalks];
+                unsigned long long old[kWalks];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) par[k] = (x[k] >= 0) ? nxt[x[k]] : -1;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) old[k] = (par[k] >= 0) ? atomicAdd(&P[par[k]], carry[k] - kChild) : 0ull;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    if (par[k] >= 0 && (old[k] >> 32) == 1ull) {
+                        carry[k] = (old[k] & 0xFFFFFFFFull) + carry[k] + 1ull;
+                        x[k] = par[k];
+                        any = true;
+                    } else {
+                        x[k] = -1;
+                    }
+                }
+                if (!any) break;
             }
         }
         __syncthreads();
         // offsets of children inside their parent's interval
-        for (int v = tid; v < n; v += BT) {
-            if (v == u) continue;
-            const int sz = (int)(P[v] & 0xFFFFFFFFull) + 1;
-            off[v] = 1 + atomicAdd(&cur[nxt[v]], sz);
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int par[kWalks];
+            int sz[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                const bool ok = v < n && v != u;
+                par[k] = ok ? nxt[v] : -1;
+                sz[k] = ok ? (int)(P[v] & 0xFFFFFFFFull) + 1 : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k)
+                if (par[k] >= 0) off[b0 + k * BT] = 1 + atomicAdd(&cur[par[k]], sz[k]);
         }
         __syncthreads();
-        // preorder numbers: walk up to the first numbered ancestor, write back
-        for (int v = tid; v < n; v += BT) {
-            if (pre[v] >= 0) continue;
-            int acc = 0, x = v, px = -1;
-            for (int guard = 0; guard < n; ++guard) {
-                px = pre[x];
-                if (px >= 0) break;
-                acc += off[x];
-                x = nxt[x];
+        // preorder numbers: walk up to the first numbered ancestor, then walk
+        // the same path again writing the numbers
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int v0[kWalks], x[kWalks], acc[kWalks], total[kWalks], stop[kWalks], ph[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                v0[k] = v;
+                x[k] = v;
+                acc[k] = 0;
+                total[k] = 0;
+                stop[k] = -1;
+                ph[k] = (v < n && pre[v] < 0) ? 0 : 2;
             }
-            const int total = px + acc;
-            int y = v, s = 0;
-            while (y != x) {
-                pre[y] = total - s;
-                s += off[y];
-                y = nxt[y];
+            for (int guard = 0; guard <= 2 * n + 2; ++guard) {
+                int pv[kWalks], ov[kWalks], nv[kWalks];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    pv[k] = (ph[k] == 0) ? pre[x[k]] : 0;
+                    ov[k] = (ph[k] < 2) ? off[x[k]] : 0;
+                    nv[k] = (ph[k] < 2) ? nxt[x[k]] : 0;
+                }
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    if (ph[k] == 0) {
+                        if (pv[k] >= 0) {
+                            total[k] = pv[k] + acc[k];
+                            stop[k] = x[k];
+                            x[k] = v0[k];
+                            acc[k] = 0;
+                            ph[k] = (v0[k] == stop[k]) ? 2 : 1;  // v0 numbered meanwhile
+                        } else {
+                            acc[k] += ov[k];
+                            x[k] = nv[k];
+                        }
+                    } else if (ph[k] == 1) {
+                        pre[x[k]] = total[k] - acc[k];
+                        acc[k] += ov[k];
+                        x[k] = nv[k];
+                        if (x[k] == stop[k]) ph[k] = 2;
+                    }
+                    any |= (ph[k] < 2);
+                }
+                if (!any) break;
             }
         }
         __syncthreads();
 
         // ---- 3. Algorithm 2 ------------------------------------------------
+        // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u. Per chunk of edges the
+        // ancestors, their successors and the tested intervals are loaded
+        // independently of each other.
         const long long c2 = clock64();
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
             const int pv = pre[v];
+            const int s0 = __ldg(p.pathptr + v);
+            const int d = __ldg(p.pathptr + v + 1) - s0;
+            int prevb = v, prevnb = nxt[v];
             int cnt = 0;
-            int b = v;
-            while (b != u) {
-                const int a = __ldg(p.bpar + b);
-                if (nxt[b] == a) {
-                    const int lo = pre[b];
-                    const int sz = (int)(P[b] & 0xFFFFFFFFull) + 1;
-                    cnt += (lo <= pv && pv < lo + sz) ? 1 : 0;
-                } else if (nxt[a] == b) {
-                    const int lo = pre[a];
-                    const int sz = (int)(P[a] & 0xFFFFFFFFull) + 1;
-                    cnt -= (lo <= pv && pv < lo + sz) ? 1 : 0;
+            for (int c = 0; c < d; c += kPathChunk) {
+                int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(p.path + s0 + c + j) : -1;
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) {
+                    const int b = (j == 0) ? prevb : a[j - 1];
+                    const int nb = (j == 0) ? prevnb : na[j - 1];
+                    tx[j] = -1;
+                    sg[j] = 0;
+                    if (a[j] >= 0) {
+                        if (nb == a[j]) {
+                            tx[j] = b;
+                            sg[j] = 1;
+                        } else if (na[j] == b) {
+                            tx[j] = a[j];
+                            sg[j] = -1;
+                        }
+                    }
                 }
-                b = a;
+                int lo[kPathChunk], sz[kPathChunk];
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) {
+                    lo[j] = (sg[j] != 0) ? pre[tx[j]] : 0;
+                    sz[j] = (sg[j] != 0) ? (int)(P[tx[j]] & 0xFFFFFFFFull) + 1 : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j)
+                    if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
+                prevb = a[kPathChunk - 1];
+                prevnb = na[kPathChunk - 1];
             }
             Rp[v] += cnt;
         }
@@ -421,8 +521,8 @@ cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 
 int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm)
 {
-    if (block_threads != 256 && block_threads != 512 && block_threads != 1024) block_threads = 512;
-    if (ctas_per_sm < 1) ctas_per_sm = (block_threads == 1024) ? 1 : 2048 / block_threads;
+    if (block_threads != 256 && block_threads != 512 && block_threads != 1024) block_threads = 1024;
+    if (ctas_per_sm < 1) ctas_per_sm = (block_threads == 1024) ? 1 : 1024 / block_threads;
     c->block_threads = block_threads;
     c->ctas = c->num_sms * ctas_per_sm;
     c->ws_stride = ((int64_t)c->n + 2 + 31) / 32 * 32;
@@ -453,6 +553,8 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     p.rp = c->d_rp;
     p.ci = c->d_ci;
     p.bpar = c->d_bpar;
+    p.path = c->d_path;
+    p.pathptr = c->d_pathptr;
     p.ws = c->d_ws;
     p.stride = c->ws_stride;
     p.Rp = c->d_Rp;
