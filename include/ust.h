@@ -121,9 +121,11 @@ typedef struct {
     double combine_ms;      /* the diagonal combination */
     int64_t last_trees;     /* trees processed by the last sampling launch */
     int64_t last_draws;     /* stack entries drawn by the last sampling launch */
-    /* SM clock cycles spent by the last sampling launch in its three phases,
-     * summed over trees: cycle popping, DFS intervals, Algorithm 2 */
-    int64_t last_phase_cycles[3];
+    /* SM clock cycles of the last sampling launch per phase, summed over
+     * trees: [0] first draws, [1] in-degrees, [2] peeling + cycle list,
+     * [3] later popping rounds, [4] subtree sizes and child offsets,
+     * [5] preorder numbers, [6] Algorithm 2, [7] whole tree */
+    int64_t last_phase_cycles[8];
 } ust_info;
 
 /* Fills *o with the defaults. */

@@ -332,7 +332,7 @@ int ust_get_info(const ust_ctx *h, ust_info *out)
     out->kernel_launches = c->launches;
     out->last_trees = c->last_trees;
     out->last_draws = c->last_draws;
-    for (int k = 0; k < 3; ++k) out->last_phase_cycles[k] = c->last_phase_cycles[k];
+    for (int k = 0; k < 8; ++k) out->last_phase_cycles[k] = c->last_phase_cycles[k];
     double *ms[Ctx::kEvPhases] = {&out->bfs_ms, &out->sample_ms, &out->reduce_ms, &out->solve_ms, &out->combine_ms};
     for (int ph = 0; ph < Ctx::kEvPhases; ++ph) {
         if (!c->ev_used[ph]) continue;

@@ -90,6 +90,19 @@ __device__ __forceinline__ int stack_entry(const SampleParams &p, int v, uint32_
 
 constexpr int kFinal = -1;  // mark of vertices known to reach u
 
+// Relaxed CTA-scope load/store: a value written by one thread of the CTA is
+// seen by the others without going through a stale L1 line.
+__device__ __forceinline__ int ld_relaxed_cta(const int32_t *ptr)
+{
+    int v;
+    asm volatile("ld.relaxed.cta.global.s32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_cta(int32_t *ptr, int v)
+{
+    asm volatile("st.relaxed.cta.global.s32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
+}
+
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
 constexpr int kPathChunk = 4;
@@ -116,11 +129,22 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err;
+    __shared__ int s_cnt, s_err, s_comp, s_abort;
     __shared__ unsigned long long s_draws;
+    __shared__ unsigned long long cyc[8];  // clock64 per phase, kept by thread 0
+    __shared__ long long tmark;
+    if (tid < 8) cyc[tid] = 0ull;
+#define UST_PHASE(k)                                    \
+    do {                                                \
+        if (tid == 0) {                                 \
+            const long long _now = clock64();           \
+            cyc[k] += (unsigned long long)(_now - tmark); \
+            tmark = _now;                               \
+        }                                               \
+    } while (0)
 
     unsigned long long my_draws = 0, my_rounds = 0;
-    unsigned long long cyc_pop = 0, cyc_int = 0, cyc_agg = 0;  // thread 0: clock64 per phase
+
     int my_max_rounds = 0, my_max_pops = 0;
 
     for (;;) {
@@ -129,7 +153,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         const long long t = s_tree;
         if (t >= p.t_end) break;
         const uint32_t tree = (uint32_t)t;
-        const long long c0 = clock64();
+        if (tid == 0) tmark = clock64();
 
         // ---- 1. cycle popping --------------------------------------------
         for (int v = tid; v < n; v += BT) {
@@ -142,8 +166,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             s_draws = (unsigned long long)(n - 1);
             s_cnt = 0;
             s_err = 0;
+            s_comp = 0;
+            s_abort = 0;
         }
         __syncthreads();
+        UST_PHASE(0);
         // in-degrees: mark is consumed by peeling, P keeps the children count
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
@@ -152,6 +179,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             atomicAdd(&P[y], kChild);
         }
         __syncthreads();
+        UST_PHASE(1);
         // round 0: peel from the leaves; a thread that removes a vertex's
         // last in-edge continues with that vertex. What is left are the
         // vertices on cycles.
@@ -182,6 +210,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         for (int v = tid; v < n; v += BT)
             if (v != u && mark[v] > 0) XA[atomicAdd(&s_cnt, 1)] = v;  // cycle vertices
         __syncthreads();
+        UST_PHASE(2);
         int nX = s_cnt;
 
         int rounds = 0;
@@ -311,6 +340,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             }
         }
         if (failed) break;
+        UST_PHASE(3);
         if (tid == 0) {
             my_draws += s_draws;
             my_rounds += (unsigned long long)rounds;
@@ -329,21 +359,24 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         __syncthreads();
 
         // ---- 2. DFS intervals ---------------------------------------------
-        const long long c1 = clock64();
         // Subtree sizes from the leaves (P[v] == 0 exactly for leaves: an
         // inner vertex always has pending children or a nonzero size sum).
+        // A child arriving at its parent gets, from the same atomic, the sizes
+        // of the siblings that arrived before it: its offset in the parent's
+        // interval. A vertex is complete when its last child arrives; the
+        // completion order is recorded reversed in ord, so every vertex comes
+        // after its parent there.
+        int32_t *ord = XB;
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
             int x[kWalks];
             unsigned long long carry[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                if (v < n) {
-                    cur[v] = 0;
-                    pre[v] = (v == u) ? 0 : -1;
-                }
+                if (v < n) pre[v] = -1;
                 x[k] = (v < n && v != u && P[v] == 0ull) ? v : -1;
                 carry[k] = 1ull;
+                if (x[k] >= 0) ord[n - 1 - atomicAdd(&s_comp, 1)] = x[k];
             }
             for (int guard = 0; guard <= n; ++guard) {
                 int par[kWalks];
@@ -355,9 +388,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
+                    if (par[k] >= 0) off[x[k]] = 1 + (int)(old[k] & 0xFFFFFFFFull);
                     if (par[k] >= 0 && (old[k] >> 32) == 1ull) {
                         carry[k] = (old[k] & 0xFFFFFFFFull) + carry[k] + 1ull;
                         x[k] = par[k];
+                        ord[n - 1 - atomicAdd(&s_comp, 1)] = x[k];
                         any = true;
                     } else {
                         x[k] = -1;
@@ -367,76 +402,39 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             }
         }
         __syncthreads();
-        // offsets of children inside their parent's interval
-        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int par[kWalks];
-            int sz[kWalks];
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                const bool ok = v < n && v != u;
-                par[k] = ok ? nxt[v] : -1;
-                sz[k] = ok ? (int)(P[v] & 0xFFFFFFFFull) + 1 : 0;
+        UST_PHASE(4);
+        // preorder numbers in that order: a vertex waits for its parent's
+        // number (bounded; the parent precedes it in ord, so the waits form
+        // no cycle) and adds its offset.
+        for (int i = tid; i < n; i += BT) {
+            const int v = ord[i];
+            if (v == u) {
+                st_relaxed_cta(pre + u, 0);
+                continue;
             }
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k)
-                if (par[k] >= 0) off[b0 + k * BT] = 1 + atomicAdd(&cur[par[k]], sz[k]);
+            const int par = nxt[v];
+            const int o = off[v];
+            int pp = ld_relaxed_cta(pre + par);
+            for (int spin = 0; pp < 0; ++spin) {
+                if (spin > (1 << 22) || *(volatile int *)&s_abort) {
+                    s_abort = 1;
+                    break;
+                }
+                pp = ld_relaxed_cta(pre + par);
+            }
+            st_relaxed_cta(pre + v, pp + o);
         }
         __syncthreads();
-        // preorder numbers: walk up to the first numbered ancestor, then walk
-        // the same path again writing the numbers
-        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int v0[kWalks], x[kWalks], acc[kWalks], total[kWalks], stop[kWalks], ph[kWalks];
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                v0[k] = v;
-                x[k] = v;
-                acc[k] = 0;
-                total[k] = 0;
-                stop[k] = -1;
-                ph[k] = (v < n && pre[v] < 0) ? 0 : 2;
-            }
-            for (int guard = 0; guard <= 2 * n + 2; ++guard) {
-                int pv[kWalks], ov[kWalks], nv[kWalks];
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    pv[k] = (ph[k] == 0) ? pre[x[k]] : 0;
-                    ov[k] = (ph[k] < 2) ? off[x[k]] : 0;
-                    nv[k] = (ph[k] < 2) ? nxt[x[k]] : 0;
-                }
-                bool any = false;
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    if (ph[k] == 0) {
-                        if (pv[k] >= 0) {
-                            total[k] = pv[k] + acc[k];
-                            stop[k] = x[k];
-                            x[k] = v0[k];
-                            acc[k] = 0;
-                            ph[k] = (v0[k] == stop[k]) ? 2 : 1;  // v0 numbered meanwhile
-                        } else {
-                            acc[k] += ov[k];
-                            x[k] = nv[k];
-                        }
-                    } else if (ph[k] == 1) {
-                        pre[x[k]] = total[k] - acc[k];
-                        acc[k] += ov[k];
-                        x[k] = nv[k];
-                        if (x[k] == stop[k]) ph[k] = 2;
-                    }
-                    any |= (ph[k] < 2);
-                }
-                if (!any) break;
-            }
+        if (s_abort) {
+            if (tid == 0) atomicOr(p.status, kStatusBadState);
+            break;
         }
-        __syncthreads();
+        UST_PHASE(5);
 
         // ---- 3. Algorithm 2 ------------------------------------------------
         // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u. Per chunk of edges the
         // ancestors, their successors and the tested intervals are loaded
         // independently of each other.
-        const long long c2 = clock64();
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
             const int pv = pre[v];
@@ -481,22 +479,21 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             Rp[v] += cnt;
         }
         __syncthreads();
+        UST_PHASE(6);
         if (tid == 0) {
-            const long long c3 = clock64();
-            cyc_pop += (unsigned long long)(c1 - c0);
-            cyc_int += (unsigned long long)(c2 - c1);
-            cyc_agg += (unsigned long long)(c3 - c2);
+            unsigned long long tot = 0ull;
+            for (int k = 0; k < 7; ++k) tot += cyc[k];
+            cyc[7] = tot;  // running total over trees
         }
     }
+#undef UST_PHASE
 
     if (tid == 0) {
         atomicAdd(p.stats + 0, my_draws);
         atomicAdd(p.stats + 1, my_rounds);
         atomicMax(p.stats + 2, (unsigned long long)my_max_rounds);
         atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
-        atomicAdd(p.stats + 8, cyc_pop);
-        atomicAdd(p.stats + 9, cyc_int);
-        atomicAdd(p.stats + 10, cyc_agg);
+        for (int k = 0; k < 8; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
     }
 }
 
@@ -606,7 +603,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     if (status) return fail(c, UST_ECUDA, "sampler reported an inconsistent state");
     c->last_trees = t1 - t0;
     c->last_draws = c->h_stats[0];
-    for (int k = 0; k < 3; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
+    for (int k = 0; k < 8; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
     if (draws) *draws = c->h_stats[0];
     if (rounds) *rounds = c->h_stats[1];
     if (max_rounds) *max_rounds = (int)c->h_stats[2];
