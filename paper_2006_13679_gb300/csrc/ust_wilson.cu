@@ -90,19 +90,6 @@ __device__ __forceinline__ int stack_entry(const SampleParams &p, int v, uint32_
 
 constexpr int kFinal = -1;  // mark of vertices known to reach u
 
-// Relaxed CTA-scope load/store: a value written by one thread of the CTA is
-// seen by the others without going through a stale L1 line.
-__device__ __forceinline__ int ld_relaxed_cta(const int32_t *ptr)
-{
-    int v;
-    asm volatile("ld.relaxed.cta.global.s32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_cta(int32_t *ptr, int v)
-{
-    asm volatile("st.relaxed.cta.global.s32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
-}
-
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
 constexpr int kPathChunk = 4;
@@ -124,12 +111,13 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     // children bookkeeping: high word = children not yet finished (the
     // children count while sampling), low word = summed subtree sizes
     unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);
-    int32_t *cur = mark, *pre = pos, *off = XA;  // interval phase reuses these
+    int32_t *off = XA;  // the interval phase reuses the round list
     int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
     constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err, s_comp, s_abort;
+    __shared__ int s_cnt, s_err, s_abort;
+    __shared__ unsigned long long s_root_sum;  // the root's children: summed subtree sizes
     __shared__ unsigned long long s_draws;
     __shared__ unsigned long long cyc[8];  // clock64 per phase, kept by thread 0
     __shared__ long long tmark;
@@ -166,49 +154,72 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             s_draws = (unsigned long long)(n - 1);
             s_cnt = 0;
             s_err = 0;
-            s_comp = 0;
             s_abort = 0;
+            s_root_sum = 0ull;
         }
         __syncthreads();
         UST_PHASE(0);
         // in-degrees: mark is consumed by peeling, P keeps the children count
-        for (int v = tid; v < n; v += BT) {
-            if (v == u) continue;
-            const int y = nxt[v];
-            atomicAdd(&mark[y], 1);
-            atomicAdd(&P[y], kChild);
+        // (the root's counters are never needed and are left alone)
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int y[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                y[k] = (v < n && v != u) ? nxt[v] : u;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                if (y[k] != u) {
+                    atomicAdd(&mark[y[k]], 1);
+                    atomicAdd(&P[y[k]], kChild);
+                }
+            }
         }
         __syncthreads();
         UST_PHASE(1);
         // round 0: peel from the leaves; a thread that removes a vertex's
         // last in-edge continues with that vertex. What is left are the
         // vertices on cycles.
+        // Each step removes the in-edge of y and fetches y's successor in the
+        // same round trip.
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int x[kWalks];
+            int y[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                x[k] = (v < n && v != u && (P[v] >> 32) == 0ull) ? v : -1;
+                const bool leaf = v < n && v != u && (P[v] >> 32) == 0ull;
+                y[k] = leaf ? nxt[v] : u;
             }
             for (int guard = 0; guard <= n; ++guard) {
-                int y[kWalks], old[kWalks];
+                int old[kWalks], ny[kWalks];
 #pragma unroll
-                for (int k = 0; k < kWalks; ++k) y[k] = (x[k] >= 0) ? nxt[x[k]] : u;
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) old[k] = (y[k] != u) ? atomicSub(&mark[y[k]], 1) : 0;
+                for (int k = 0; k < kWalks; ++k) {
+                    old[k] = (y[k] != u) ? atomicSub(&mark[y[k]], 1) : 0;
+                    ny[k] = (y[k] != u) ? nxt[y[k]] : u;
+                }
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    x[k] = (old[k] == 1) ? y[k] : -1;
-                    any |= (x[k] >= 0);
+                    y[k] = (old[k] == 1) ? ny[k] : u;  // y peeled: remove its out-edge next
+                    any |= (y[k] != u);
                 }
                 if (!any) break;
             }
         }
         __syncthreads();
         if (tid == 0) mark[u] = kFinal;
-        for (int v = tid; v < n; v += BT)
-            if (v != u && mark[v] > 0) XA[atomicAdd(&s_cnt, 1)] = v;  // cycle vertices
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int m[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                m[k] = (v < n && v != u) ? mark[v] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k)
+                if (m[k] > 0) XA[atomicAdd(&s_cnt, 1)] = b0 + k * BT;  // cycle vertices
+        }
         __syncthreads();
         UST_PHASE(2);
         int nX = s_cnt;
@@ -239,8 +250,8 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 nxt[x] = y;
                 mark[x] = rounds;
                 pos[x] = i;
-                atomicAdd(&P[old], 0ull - kChild);
-                atomicAdd(&P[y], kChild);
+                if (old != u) atomicAdd(&P[old], 0ull - kChild);
+                if (y != u) atomicAdd(&P[y], kChild);
             }
             __syncthreads();
             // (b) S(x): first redrawn vertex or known-final vertex after x
@@ -249,9 +260,10 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 int res = -2;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = mark[y];
+                    const int ny = nxt[y];
                     if (m == kFinal) { res = -1; break; }
                     if (m == rounds) { res = pos[y]; break; }
-                    y = nxt[y];
+                    y = ny;
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
@@ -362,40 +374,48 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         // Subtree sizes from the leaves (P[v] == 0 exactly for leaves: an
         // inner vertex always has pending children or a nonzero size sum).
         // A child arriving at its parent gets, from the same atomic, the sizes
-        // of the siblings that arrived before it: its offset in the parent's
-        // interval. A vertex is complete when its last child arrives; the
-        // completion order is recorded reversed in ord, so every vertex comes
-        // after its parent there.
-        int32_t *ord = XB;
+        // of the siblings that arrived before it: its offset inside the
+        // parent's interval. Each step issues the atomic at the parent and the
+        // load of the parent's parent together. The root's sum lives in shared
+        // memory.
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int x[kWalks];
+            int x[kWalks], par[kWalks];
             unsigned long long carry[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                if (v < n) pre[v] = -1;
-                x[k] = (v < n && v != u && P[v] == 0ull) ? v : -1;
+                const bool leaf = v < n && v != u && P[v] == 0ull;
+                x[k] = leaf ? v : -1;
+                par[k] = leaf ? nxt[v] : -1;
                 carry[k] = 1ull;
-                if (x[k] >= 0) ord[n - 1 - atomicAdd(&s_comp, 1)] = x[k];
             }
             for (int guard = 0; guard <= n; ++guard) {
-                int par[kWalks];
                 unsigned long long old[kWalks];
+                int gp[kWalks];
 #pragma unroll
-                for (int k = 0; k < kWalks; ++k) par[k] = (x[k] >= 0) ? nxt[x[k]] : -1;
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) old[k] = (par[k] >= 0) ? atomicAdd(&P[par[k]], carry[k] - kChild) : 0ull;
+                for (int k = 0; k < kWalks; ++k) {
+                    old[k] = 0ull;
+                    gp[k] = -1;
+                    if (par[k] == u) {
+                        old[k] = atomicAdd(&s_root_sum, carry[k]);
+                    } else if (par[k] >= 0) {
+                        old[k] = atomicAdd(&P[par[k]], carry[k] - kChild);
+                        gp[k] = nxt[par[k]];
+                    }
+                }
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    if (par[k] >= 0) off[x[k]] = 1 + (int)(old[k] & 0xFFFFFFFFull);
-                    if (par[k] >= 0 && (old[k] >> 32) == 1ull) {
+                    if (par[k] < 0) continue;
+                    off[x[k]] = 1 + (int)(old[k] & 0xFFFFFFFFull);
+                    if (par[k] != u && (old[k] >> 32) == 1ull) {
                         carry[k] = (old[k] & 0xFFFFFFFFull) + carry[k] + 1ull;
                         x[k] = par[k];
-                        ord[n - 1 - atomicAdd(&s_comp, 1)] = x[k];
+                        par[k] = gp[k];
                         any = true;
                     } else {
                         x[k] = -1;
+                        par[k] = -1;
                     }
                 }
                 if (!any) break;
@@ -403,30 +423,57 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         }
         __syncthreads();
         UST_PHASE(4);
-        // preorder numbers in that order: a vertex waits for its parent's
-        // number (bounded; the parent precedes it in ord, so the waits form
-        // no cycle) and adds its offset.
-        for (int i = tid; i < n; i += BT) {
-            const int v = ord[i];
-            if (v == u) {
-                st_relaxed_cta(pre + u, 0);
-                continue;
+        // preorder numbers: pre[v] = sum of the offsets on the path from v up
+        // to u, by pointer jumping on packed (ancestor, partial sum) words.
+        // Updates are in place: a word read while its owner rewrites it is
+        // either the old or the new consistent pair, both valid.
+        unsigned long long *JA = reinterpret_cast<unsigned long long *>(J0);  // J0, J1
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int pa[kWalks], of[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                const bool ok = v < n && v != u;
+                pa[k] = ok ? nxt[v] : u;
+                of[k] = ok ? off[v] : 0;
             }
-            const int par = nxt[v];
-            const int o = off[v];
-            int pp = ld_relaxed_cta(pre + par);
-            for (int spin = 0; pp < 0; ++spin) {
-                if (spin > (1 << 22) || *(volatile int *)&s_abort) {
-                    s_abort = 1;
-                    break;
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                if (v < n) JA[v] = ((unsigned long long)(uint32_t)pa[k] << 32) | (uint32_t)of[k];
+            }
+        }
+        __syncthreads();
+        for (int step = 0; step < p.max_steps + 2; ++step) {
+            int pending = 0;
+            for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+                unsigned long long a[kWalks], b[kWalks];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int v = b0 + k * BT;
+                    a[k] = (v < n) ? JA[v] : ((unsigned long long)(uint32_t)u << 32);
                 }
-                pp = ld_relaxed_cta(pre + par);
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int j = (int)(a[k] >> 32);
+                    b[k] = (j != u) ? JA[j] : 0ull;
+                }
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int j = (int)(a[k] >> 32);
+                    if (j == u) continue;
+                    const uint32_t j2 = (uint32_t)(b[k] >> 32);
+                    const uint32_t sum = (uint32_t)a[k] + (uint32_t)b[k];
+                    JA[b0 + k * BT] = ((unsigned long long)j2 << 32) | sum;
+                    pending |= ((int)j2 != u);
+                }
             }
-            st_relaxed_cta(pre + v, pp + o);
+            if (!__syncthreads_or(pending)) break;
+            if (step == p.max_steps + 1) s_abort = 1;
         }
         __syncthreads();
         if (s_abort) {
-            if (tid == 0) atomicOr(p.status, kStatusBadState);
+            if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
             break;
         }
         UST_PHASE(5);
@@ -437,7 +484,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         // independently of each other.
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
-            const int pv = pre[v];
+            const int pv = (int)(uint32_t)JA[v];
             const int s0 = __ldg(p.pathptr + v);
             const int d = __ldg(p.pathptr + v + 1) - s0;
             int prevb = v, prevnb = nxt[v];
@@ -467,7 +514,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 int lo[kPathChunk], sz[kPathChunk];
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j) {
-                    lo[j] = (sg[j] != 0) ? pre[tx[j]] : 0;
+                    lo[j] = (sg[j] != 0) ? (int)(uint32_t)JA[tx[j]] : 0;
                     sz[j] = (sg[j] != 0) ? (int)(P[tx[j]] & 0xFFFFFFFFull) + 1 : 0;
                 }
 #pragma unroll
