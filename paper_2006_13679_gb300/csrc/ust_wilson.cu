@@ -90,6 +90,18 @@ __device__ __forceinline__ int stack_entry(const SampleParams &p, int v, uint32_
 
 constexpr int kFinal = -1;  // mark of vertices known to reach u
 
+// Appends val to q (length counter *cnt in shared memory) for the lanes with
+// flag set; one shared atomic per warp. All 32 lanes must call it.
+__device__ __forceinline__ void warp_append(bool flag, int val, int32_t *q, int *cnt)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (flag) q[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
 constexpr int kPathChunk = 4;
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err, s_abort;
+    __shared__ int s_cnt, s_err, s_abort, s_qn, s_qh;
     __shared__ unsigned long long s_root_sum;  // the root's children: summed subtree sizes
     __shared__ unsigned long long s_draws;
     __shared__ unsigned long long cyc[8];  // clock64 per phase, kept by thread 0
@@ -180,18 +192,39 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         UST_PHASE(1);
         // round 0: peel from the leaves; a thread that removes a vertex's
         // last in-edge continues with that vertex. What is left are the
-        // vertices on cycles.
-        // Each step removes the in-edge of y and fetches y's successor in the
-        // same round trip.
-        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+        // vertices on cycles. The successors of the leaves are queued first;
+        // every thread keeps kWalks walks in flight and refills a finished
+        // walk from the queue (one entry prefetched). Each step removes the
+        // in-edge of y and fetches y's successor in the same round trip.
+        {
+            int32_t *Q = L0;  // free until the popping rounds
+            if (tid == 0) {
+                s_qn = 0;
+                s_qh = 0;
+            }
+            __syncthreads();
+            const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
+            for (int it = 0; it < iters; ++it) {
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int v = tid + (it * kWalks + k) * BT;
+                    const bool leaf = v < n && v != u && (P[v] >> 32) == 0ull;
+                    const int y0 = leaf ? nxt[v] : u;
+                    warp_append(leaf && y0 != u, y0, Q, &s_qn);
+                }
+            }
+            __syncthreads();
+            const int qn = s_qn;
+            int idx = atomicAdd(&s_qh, 1);
+            int spare = (idx < qn) ? Q[idx] : u;
             int y[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                const bool leaf = v < n && v != u && (P[v] >> 32) == 0ull;
-                y[k] = leaf ? nxt[v] : u;
+                y[k] = spare;
+                idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
+                spare = (idx < qn) ? Q[idx] : u;
             }
-            for (int guard = 0; guard <= n; ++guard) {
+            for (int guard = 0; guard <= 2 * n + 2; ++guard) {
                 int old[kWalks], ny[kWalks];
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
@@ -201,7 +234,13 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    y[k] = (old[k] == 1) ? ny[k] : u;  // y peeled: remove its out-edge next
+                    if (y[k] != u && old[k] == 1) {
+                        y[k] = ny[k];  // y peeled: remove its out-edge next
+                    } else {
+                        y[k] = spare;
+                        idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
+                        spare = (idx < qn) ? Q[idx] : u;
+                    }
                     any |= (y[k] != u);
                 }
                 if (!any) break;
@@ -378,18 +417,45 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         // parent's interval. Each step issues the atomic at the parent and the
         // load of the parent's parent together. The root's sum lives in shared
         // memory.
-        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+        {
+            unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(J0);  // (leaf, parent) pairs
+            if (tid == 0) {
+                s_qn = 0;
+                s_qh = 0;
+            }
+            __syncthreads();
+            const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
+            for (int it = 0; it < iters; ++it) {
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int v = tid + (it * kWalks + k) * BT;
+                    const bool leaf = v < n && v != u && P[v] == 0ull;
+                    const unsigned m = __ballot_sync(0xffffffffu, leaf);
+                    const unsigned lane = threadIdx.x & 31u;
+                    int b = 0;
+                    if (lane == 0 && m) b = atomicAdd(&s_qn, __popc(m));
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    if (leaf)
+                        Q2[b + __popc(m & ((1u << lane) - 1u))] =
+                            ((unsigned long long)(uint32_t)v << 32) | (uint32_t)nxt[v];
+                }
+            }
+            __syncthreads();
+            const int qn = s_qn;
+            const unsigned long long kNone = ~0ull;
+            int idx = atomicAdd(&s_qh, 1);
+            unsigned long long spare = (idx < qn) ? Q2[idx] : kNone;
             int x[kWalks], par[kWalks];
             unsigned long long carry[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                const bool leaf = v < n && v != u && P[v] == 0ull;
-                x[k] = leaf ? v : -1;
-                par[k] = leaf ? nxt[v] : -1;
+                x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
+                par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
                 carry[k] = 1ull;
+                idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
+                spare = (idx < qn) ? Q2[idx] : kNone;
             }
-            for (int guard = 0; guard <= n; ++guard) {
+            for (int guard = 0; guard <= 2 * n + 2; ++guard) {
                 unsigned long long old[kWalks];
                 int gp[kWalks];
 #pragma unroll
@@ -406,17 +472,21 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    if (par[k] < 0) continue;
-                    off[x[k]] = 1 + (int)(old[k] & 0xFFFFFFFFull);
-                    if (par[k] != u && (old[k] >> 32) == 1ull) {
-                        carry[k] = (old[k] & 0xFFFFFFFFull) + carry[k] + 1ull;
-                        x[k] = par[k];
-                        par[k] = gp[k];
-                        any = true;
-                    } else {
-                        x[k] = -1;
-                        par[k] = -1;
+                    if (par[k] >= 0) {
+                        off[x[k]] = 1 + (int)(old[k] & 0xFFFFFFFFull);
+                        if (par[k] != u && (old[k] >> 32) == 1ull) {
+                            carry[k] = (old[k] & 0xFFFFFFFFull) + carry[k] + 1ull;
+                            x[k] = par[k];
+                            par[k] = gp[k];
+                        } else {
+                            x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
+                            par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
+                            carry[k] = 1ull;
+                            idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
+                            spare = (idx < qn) ? Q2[idx] : kNone;
+                        }
                     }
+                    any |= (par[k] >= 0);
                 }
                 if (!any) break;
             }
