@@ -186,6 +186,32 @@ UST_API int ust_sample_trees(ust_ctx *c, int64_t t0, int32_t count, uint64_t see
 /* Counters of the committed state. */
 UST_API int ust_get_info(const ust_ctx *c, ust_info *out);
 
+/* Tree counts without any allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * whose device memory belongs to another allocator that must account for
+ * every byte (a framework's caching allocator, a fixed memory budget) or code
+ * that may not allocate after start-up.
+ *
+ * Computes B_u of pivot u, then samples trees [t0, t1) under `seed` and
+ * graph_id and writes their Algorithm 2 counts to R_out (n int64, device
+ * pointer, overwritten): the same values as ust_tree_range_counts on a
+ * context for this graph, pivot and graph_id. row_ptr and col_idx are device
+ * pointers to a CSR obeying the ust_csr contract (not validated here).
+ * stream is a cudaStream_t or NULL; the call synchronises it before returning.
+ *
+ * All scratch lives in one fixed device array inside the library (about
+ * 8.5 MB, held on every GPU that loads the library until the process exits).
+ * Limits: n <= 4096 and f^c(u) = sum_v dist(u, v) <= 262144; larger inputs
+ * return UST_EINVAL before any work. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. Every call reuses the same
+ * array and overwrites what the previous call left there, so calls that can
+ * overlap on the GPU (other streams, other host threads) race: serialise them.
+ * Errors: UST_EINVAL, UST_ENOTCONNECTED, UST_ETIMEOUT, UST_ECUDA. */
+UST_API int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t nnz,
+                                    int32_t pivot, int64_t t0, int64_t t1, uint64_t seed, int32_t graph_id,
+                                    int64_t *R_out, void *stream);
+
 /* Static description of the last error of this context (never NULL). */
 UST_API const char *ust_last_error(const ust_ctx *c);
 

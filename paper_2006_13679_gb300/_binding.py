@@ -74,6 +74,9 @@ _SIGNATURES = {
     "ust_sample_trees": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "ust_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ust_info)]),
+    "ust_tree_counts_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                               ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "ust_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ust_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ust_free": (None, [ctypes.c_void_p]),

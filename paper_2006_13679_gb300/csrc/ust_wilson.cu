@@ -33,6 +33,7 @@
 //     upwards above v. Counts go to the CTA's partial row Rp; a second kernel
 //     sums the partial rows into the int64 R exactly.
 #include <algorithm>
+#include <mutex>
 
 #include "ust_common.cuh"
 
@@ -729,3 +730,211 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
 }
 
 }  // namespace ust
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the tree counts (ust_tree_counts_noalloc).
+//
+// Some callers cannot call cudaMalloc: code whose device memory belongs to
+// another allocator that must account for every byte (a framework's caching
+// allocator, a fixed memory budget), or code that may not allocate once it
+// has started. This variant runs B_u, the flattened BFS paths, the sampler
+// and the count reduction entirely in one file-scope device array of fixed
+// size; the caller passes only its inputs and its output.
+//
+// Limits: n <= kNoAllocMaxN vertices and f^c(u) = sum_v dist(u, v) <=
+// kNoAllocMaxPath. The array is about 8.5 MB and stays resident on every GPU
+// that loads this library until the process exits. Every call reuses it and
+// overwrites the previous contents, so calls that overlap on the GPU (two
+// streams, two host threads) race and must be serialised by the caller.
+namespace ust {
+namespace {
+
+constexpr int kNoAllocMaxN = 4096;
+constexpr int kNoAllocMaxPath = 262144;
+constexpr int kNoAllocCtas = 32;
+constexpr int kNoAllocThreads = 256;
+constexpr long long kNoAllocStride = ((kNoAllocMaxN + 2 + 31) / 32) * 32;
+// layout in int32 words: sampler workspace | partial counts | dist | bfs parent
+//                        | path offsets | paths | stats (16 x int64)
+constexpr long long kNaWs = 0;
+constexpr long long kNaRp = kNaWs + (long long)kNoAllocCtas * kWsArrays * kNoAllocStride;
+constexpr long long kNaDist = kNaRp + (long long)kNoAllocCtas * kNoAllocMaxN;
+constexpr long long kNaBpar = kNaDist + kNoAllocMaxN;
+constexpr long long kNaPathPtr = kNaBpar + kNoAllocMaxN;
+constexpr long long kNaPath = kNaPathPtr + ((kNoAllocMaxN + 1 + 31) / 32) * 32;
+constexpr long long kNaStats = kNaPath + kNoAllocMaxPath;
+constexpr long long kNaWords = kNaStats + 2 * 16;
+
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNaWords];
+
+// One CTA: B_u by level-synchronous pull BFS (smallest-id parent), the
+// connectivity check, f^c(u), the exclusive prefix of dist into pathptr and
+// the flattened paths. Errors go to status (bit 1: disconnected, bit 2: too
+// many path entries).
+constexpr int kPrepThreads = 1024;
+__global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, int u, const int32_t *__restrict__ rp,
+                                                                       const int32_t *__restrict__ ci, int32_t *dist,
+                                                                       int32_t *bpar, int32_t *pathptr, int32_t *path,
+                                                                       int path_cap, int *status)
+{
+    __shared__ int s_warp[kPrepThreads / 32 + 1];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int v = tid; v < n; v += kPrepThreads) {
+        dist[v] = (v == u) ? 0 : -1;
+        bpar[v] = -1;
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int level = 0; level < n; ++level) {
+        int any = 0;
+        for (int v = tid; v < n; v += kPrepThreads) {
+            if (dist[v] >= 0) continue;
+            for (int e = rp[v]; e < rp[v + 1]; ++e) {
+                const int w = ci[e];
+                if (dist[w] == level) {
+                    dist[v] = level + 1;
+                    bpar[v] = w;
+                    any = 1;
+                    break;
+                }
+            }
+        }
+        if (!__syncthreads_or(any)) break;
+    }
+    // exclusive prefix of dist (unreached vertices flag the graph as disconnected)
+    int carry = 0;
+    for (int base = 0; base < n; base += kPrepThreads) {
+        const int i = base + tid;
+        const int d = (i < n) ? dist[i] : 0;
+        if (d < 0) s_bad = 1;
+        const int x = d > 0 ? d : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int w = s_warp[lane];
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s_warp[lane] = wi - w;
+            if (lane == 31) s_warp[32] = wi;
+        }
+        __syncthreads();
+        if (i < n) pathptr[i] = carry + s_warp[wid] + incl - x;
+        carry += s_warp[32];
+        __syncthreads();
+    }
+    if (tid == 0) pathptr[n] = carry;
+    if (s_bad || carry > path_cap) {
+        if (tid == 0) *status |= s_bad ? 1 : 2;
+        return;
+    }
+    __syncthreads();
+    for (int v = tid; v < n; v += kPrepThreads) {
+        int k = pathptr[v];
+        const int end = pathptr[v + 1];
+        int x = v;
+        while (x != u && k < end) {
+            x = bpar[x];
+            path[k++] = x;
+        }
+    }
+}
+
+// Device address of g_noalloc_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+int32_t *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+}  // namespace
+
+}  // namespace ust
+
+extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t nnz,
+                                       int32_t pivot, int64_t t0, int64_t t1, uint64_t seed, int32_t graph_id,
+                                       int64_t *R_out, void *stream)
+{
+    using namespace ust;
+    if (!row_ptr || !col_idx || !R_out || n < 2 || nnz < 2 || pivot < 0 || pivot >= n || t0 < 0 || t1 < t0 ||
+        t1 > (int64_t)0xFFFFFFFFll)
+        return UST_EINVAL;
+    if (n > kNoAllocMaxN) return UST_EINVAL;  // beyond the fixed scratch array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return UST_ECUDA;
+    int32_t *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return UST_ECUDA;
+            g_noalloc_ptr[dev] = static_cast<int32_t *>(ptr);
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int32_t *ws = base + kNaWs, *Rp = base + kNaRp, *dist = base + kNaDist, *bpar = base + kNaBpar;
+    int32_t *pathptr = base + kNaPathPtr, *path = base + kNaPath;
+    unsigned long long *stats = reinterpret_cast<unsigned long long *>(base + kNaStats);
+    // the previous call's contents stay in the array: clear what must start at zero
+    if (cudaMemsetAsync(stats, 0, 16 * sizeof(unsigned long long), st) != cudaSuccess) return UST_ECUDA;
+    if (cudaMemsetAsync(Rp, 0, (size_t)kNoAllocCtas * n * sizeof(int32_t), st) != cudaSuccess) return UST_ECUDA;
+    if (cudaMemsetAsync(R_out, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess) return UST_ECUDA;
+    int *status = reinterpret_cast<int *>(stats + 5);
+    noalloc_prepare_kernel<<<1, kPrepThreads, 0, st>>>(n, pivot, row_ptr, col_idx, dist, bpar, pathptr, path,
+                                                        kNoAllocMaxPath, status);
+    if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
+    unsigned long long h_stats[16];
+    if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess) return UST_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return UST_ECUDA;
+    if (h_stats[5] & 1) return UST_ENOTCONNECTED;
+    if (h_stats[5] & 2) return UST_EINVAL;  // f^c(u) beyond the fixed scratch array
+    int ecc = 0;
+    if (t1 > t0) {
+        ecc = n;  // upper bound on ecc(u), used only for the popping-round limit
+        SampleParams p;
+        p.n = n;
+        p.u = pivot;
+        p.graph = (uint32_t)graph_id;
+        p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+        p.key1 = (uint32_t)(seed >> 32);
+        p.rp = row_ptr;
+        p.ci = col_idx;
+        p.bpar = bpar;
+        p.path = path;
+        p.pathptr = pathptr;
+        p.ws = ws;
+        p.stride = kNoAllocStride;
+        p.Rp = Rp;
+        p.t_begin = t0;
+        p.t_end = t1;
+        p.next_tree = stats + 4;
+        p.stats = stats;
+        p.status = status;
+        p.max_rounds = (int)std::min<int64_t>(16ll * ((int64_t)nnz * ecc + n) + 1024, 1ll << 30);
+        int lg = 0;
+        while ((1ll << lg) < (long long)n) ++lg;
+        p.max_steps = lg + 4;
+        p.mode = 0;
+        p.next_out = nullptr;
+        p.pops_out = nullptr;
+        const int grid = (int)std::min<int64_t>(kNoAllocCtas, t1 - t0);
+        if (launch_sampler<kNoAllocThreads>(grid, st, p) != cudaSuccess) return UST_ECUDA;
+        reduce_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, grid, Rp, reinterpret_cast<long long *>(R_out));
+        if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
+        if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return UST_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return UST_ECUDA;
+        if (h_stats[5] & (kStatusPopRounds | kStatusJumpSteps)) return UST_ETIMEOUT;
+        if (h_stats[5]) return UST_ECUDA;
+    }
+    return UST_OK;
+}
