@@ -107,9 +107,14 @@ __device__ __forceinline__ void warp_append(bool flag, int val, int32_t *q, int 
 constexpr int kWalks = 4;
 constexpr int kPathChunk = 4;
 
-template <int BT>
+// SM = true: the per-tree counters live in shared memory (n words, n < 2^16):
+// in-degrees as "total | remaining" 16-bit halves, then the popping rounds'
+// marks, then "pending children | size sum" 16-bit halves. SM = false: the
+// same counters in global memory, 32-bit halves of a 64-bit word.
+template <int BT, bool SM>
 __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 {
+    extern __shared__ uint32_t s_dyn[];
     const int n = p.n, u = p.u, tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
@@ -125,6 +130,9 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     // children count while sampling), low word = summed subtree sizes
     unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);
     int32_t *off = XA;  // the interval phase reuses the round list
+    int32_t *rmark = SM ? reinterpret_cast<int32_t *>(s_dyn) : mark;  // marks of the popping rounds
+    uint32_t *C = s_dyn;                                           // shared counters (SM only)
+    constexpr uint32_t kC16 = 1u << 16;
     int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
     constexpr unsigned long long kChild = 1ull << 32;
 
@@ -159,8 +167,12 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         // ---- 1. cycle popping --------------------------------------------
         for (int v = tid; v < n; v += BT) {
             pop[v] = 0;
-            mark[v] = 0;
-            P[v] = 0ull;
+            if (SM) {
+                C[v] = 0u;
+            } else {
+                mark[v] = 0;
+                P[v] = 0ull;
+            }
             nxt[v] = (v == u) ? -1 : stack_entry(p, v, 0u, tree);
         }
         if (tid == 0) {
@@ -184,8 +196,12 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 if (y[k] != u) {
-                    atomicAdd(&mark[y[k]], 1);
-                    atomicAdd(&P[y[k]], kChild);
+                    if (SM) {
+                        atomicAdd(&C[y[k]], kC16 + 1u);  // total and remaining in-degree
+                    } else {
+                        atomicAdd(&mark[y[k]], 1);
+                        atomicAdd(&P[y[k]], kChild);
+                    }
                 }
             }
         }
@@ -209,7 +225,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     const int v = tid + (it * kWalks + k) * BT;
-                    const bool leaf = v < n && v != u && (P[v] >> 32) == 0ull;
+                    const bool leaf = v < n && v != u && (SM ? (C[v] >> 16) == 0u : (P[v] >> 32) == 0ull);
                     const int y0 = leaf ? nxt[v] : u;
                     warp_append(leaf && y0 != u, y0, Q, &s_qn);
                 }
@@ -229,7 +245,10 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 int old[kWalks], ny[kWalks];
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    old[k] = (y[k] != u) ? atomicSub(&mark[y[k]], 1) : 0;
+                    if (SM)
+                        old[k] = (y[k] != u) ? (int)(atomicSub(&C[y[k]], 1u) & 0xFFFFu) : 0;
+                    else
+                        old[k] = (y[k] != u) ? atomicSub(&mark[y[k]], 1) : 0;
                     ny[k] = (y[k] != u) ? nxt[y[k]] : u;
                 }
                 bool any = false;
@@ -248,19 +267,23 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             }
         }
         __syncthreads();
-        if (tid == 0) mark[u] = kFinal;
+        if (!SM && tid == 0) mark[u] = kFinal;
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
             int m[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                m[k] = (v < n && v != u) ? mark[v] : 0;
+                m[k] = (v < n && v != u) ? (SM ? (int)(C[v] & 0xFFFFu) : mark[v]) : 0;
             }
 #pragma unroll
             for (int k = 0; k < kWalks; ++k)
                 if (m[k] > 0) XA[atomicAdd(&s_cnt, 1)] = b0 + k * BT;  // cycle vertices
         }
         __syncthreads();
+        if (SM) {  // the shared words now hold the rounds' marks
+            for (int v = tid; v < n; v += BT) rmark[v] = (v == u) ? kFinal : 0;
+            __syncthreads();
+        }
         UST_PHASE(2);
         int nX = s_cnt;
 
@@ -288,10 +311,12 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 const int y = stack_entry(p, x, (uint32_t)k, tree);
                 pop[x] = k;
                 nxt[x] = y;
-                mark[x] = rounds;
+                rmark[x] = rounds;
                 pos[x] = i;
-                if (old != u) atomicAdd(&P[old], 0ull - kChild);
-                if (y != u) atomicAdd(&P[y], kChild);
+                if (!SM) {
+                    if (old != u) atomicAdd(&P[old], 0ull - kChild);
+                    if (y != u) atomicAdd(&P[y], kChild);
+                }
             }
             __syncthreads();
             // (b) S(x): first redrawn vertex or known-final vertex after x
@@ -299,7 +324,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 int y = nxt[X[i]];
                 int res = -2;
                 for (int guard = 0; guard <= n; ++guard) {
-                    const int m = mark[y];
+                    const int m = rmark[y];
                     const int ny = nxt[y];
                     if (m == kFinal) { res = -1; break; }
                     if (m == rounds) { res = pos[y]; break; }
@@ -351,9 +376,9 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 if (li == -1) {
                     int y = X[i];
                     for (int guard = 0; guard <= n; ++guard) {
-                        mark[y] = kFinal;
+                        rmark[y] = kFinal;
                         y = nxt[y];
-                        const int m = mark[y];
+                        const int m = rmark[y];
                         if (m == kFinal || m == rounds) break;
                     }
                 } else if (li == i) {
@@ -379,7 +404,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 for (int guard = 0; guard <= n; ++guard) {
                     Xn[atomicAdd(&s_cnt, 1)] = y;
                     y = nxt[y];
-                    if (mark[y] == rounds) break;
+                    if (rmark[y] == rounds) break;
                 }
             }
             __syncthreads();
@@ -411,6 +436,22 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         __syncthreads();
 
         // ---- 2. DFS intervals ---------------------------------------------
+        if (SM) {  // the shared words now count children and sum their sizes
+            for (int v = tid; v < n; v += BT) C[v] = 0u;
+            __syncthreads();
+            for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+                int y[kWalks];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int v = b0 + k * BT;
+                    y[k] = (v < n && v != u) ? nxt[v] : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k)
+                    if (y[k] >= 0) atomicAdd(&C[y[k]], kC16);
+            }
+            __syncthreads();
+        }
         // Subtree sizes from the leaves (P[v] == 0 exactly for leaves: an
         // inner vertex always has pending children or a nonzero size sum).
         // A child arriving at its parent gets, from the same atomic, the sizes
@@ -430,7 +471,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     const int v = tid + (it * kWalks + k) * BT;
-                    const bool leaf = v < n && v != u && P[v] == 0ull;
+                    const bool leaf = v < n && v != u && (SM ? C[v] == 0u : P[v] == 0ull);
                     const unsigned m = __ballot_sync(0xffffffffu, leaf);
                     const unsigned lane = threadIdx.x & 31u;
                     int b = 0;
@@ -463,7 +504,14 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 for (int k = 0; k < kWalks; ++k) {
                     old[k] = 0ull;
                     gp[k] = -1;
-                    if (par[k] == u) {
+                    if (SM) {
+                        // repack the 16|16 word as 32|32 so the code below is shared
+                        if (par[k] >= 0) {
+                            const uint32_t o = atomicAdd(&C[par[k]], (uint32_t)carry[k] - kC16);
+                            old[k] = ((unsigned long long)(o >> 16) << 32) | (o & 0xFFFFu);
+                            if (par[k] != u) gp[k] = nxt[par[k]];
+                        }
+                    } else if (par[k] == u) {
                         old[k] = atomicAdd(&s_root_sum, carry[k]);
                     } else if (par[k] >= 0) {
                         old[k] = atomicAdd(&P[par[k]], carry[k] - kChild);
@@ -586,7 +634,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j) {
                     lo[j] = (sg[j] != 0) ? (int)(uint32_t)JA[tx[j]] : 0;
-                    sz[j] = (sg[j] != 0) ? (int)(P[tx[j]] & 0xFFFFFFFFull) + 1 : 0;
+                    sz[j] = (sg[j] != 0) ? (SM ? (int)(C[tx[j]] & 0xFFFFu) : (int)(P[tx[j]] & 0xFFFFFFFFull)) + 1 : 0;
                 }
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j)
@@ -625,10 +673,22 @@ __global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict_
     }
 }
 
+// Shared counters for graphs of at most this many vertices (4 B each, below
+// 2^16 so that two 16-bit halves fit one word).
+constexpr int kSmemMaxN = 56 * 1024;
+
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
-    sample_aggregate_kernel<BT><<<grid, BT, 0, st>>>(p);
+    if (p.n <= kSmemMaxN) {
+        const size_t bytes = (size_t)p.n * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(sample_aggregate_kernel<BT, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        sample_aggregate_kernel<BT, true><<<grid, BT, bytes, st>>>(p);
+    } else {
+        sample_aggregate_kernel<BT, false><<<grid, BT, 0, st>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -237,3 +237,22 @@ def test_repeat_runs_are_identical(pkg):
         b.sample_aggregate(300, 11)
         assert np.array_equal(a.counts(), b.counts())
         assert np.array_equal(a.diag(), b.diag())
+
+
+@pytest.mark.parametrize("maker", [lambda: synth.ba(70000, 3, seed=9), lambda: synth.rmat(17, 8, seed=2)])
+def test_counts_above_shared_memory_limit(pkg, orc, maker):
+    """Graphs with more than 56k vertices keep their per-tree counters in
+    global memory instead of shared memory: R bit-exact as well."""
+    g = maker()
+    assert g.n > 56 * 1024
+    u = synth.max_degree_vertex(g)
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(300, 21)
+        _, _, par = orc.bfs(g, u)
+        R_ref, steps = orc.sample_aggregate(g, u, par, 0, 300, 21, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert h.info()["draws"] == steps
+        nxt, pops = h.sample_trees(100, 3, 21, with_pops=True)
+        for i in range(3):
+            ref, ref_pops, _ = orc.wilson(g, u, 100 + i, 21)
+            assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
