@@ -663,6 +663,474 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same three phases for graphs of at most kSmemMaxN vertices (ids below
+// 2^16), with the hot per-tree state in shared memory (4 bytes per vertex,
+// one n-word array whose view changes per phase):
+//   peeling   16-bit remaining in-degree | 16-bit successor
+//   rounds    16-bit round mark          | 16-bit successor
+//   sizes     32-bit word: pending children << 16 | summed sizes
+//   preorder  32-bit word: ancestor << 16 | summed offsets
+// The tree's parent array, stack depths, round lists, offsets and sizes stay
+// in the CTA's global workspace. 16-bit counters share a 32-bit word with a
+// neighbour and are updated by adding or subtracting 1 << 16 * (v & 1); a
+// count never passes below 0 or above n - 1, so halves never carry.
+constexpr uint16_t kFinal16 = 0xFFFFu;
+constexpr int kMaxStamp16 = 0xFFFE;
+
+__device__ __forceinline__ uint32_t half_add(uint32_t *words, int v, int delta)
+{
+    const int sh = (v & 1) << 4;
+    const uint32_t old = atomicAdd(words + (v >> 1), (uint32_t)delta << sh);
+    return (old >> sh) & 0xFFFFu;
+}
+
+template <int BT>
+__global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams p)
+{
+    extern __shared__ uint32_t s_dyn[];
+    const int n = p.n, u = p.u, tid = threadIdx.x;
+    const int nhalf = (n + 1) >> 1;          // 32-bit words of one 16-bit array
+    uint16_t *lo16 = reinterpret_cast<uint16_t *>(s_dyn);        // counts, then marks
+    uint32_t *lo32 = s_dyn;                                      // the same, as words
+    uint16_t *nx16 = reinterpret_cast<uint16_t *>(s_dyn + nhalf);  // successors
+    uint32_t *C = s_dyn;                                         // sizes / preorder words
+    const long long S_ = p.stride;
+    int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
+    int32_t *nxt = base;              // the tree's parent array at the end
+    int32_t *pop = base + 1 * S_;     // stack depth of the current top
+    int32_t *gsz = base + 2 * S_;     // subtree sizes (for Algorithm 2)
+    int32_t *pos = base + 3 * S_;     // index of a redrawn vertex in the round's list
+    int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;
+    int32_t *Sx = base + 6 * S_;
+    int32_t *J0 = base + 7 * S_, *J1 = base + 8 * S_;
+    int32_t *L0 = base + 9 * S_, *L1 = base + 10 * S_;
+    unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(base + 11 * S_);  // leaf queue
+    int32_t *off = XA;
+    int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
+    constexpr uint32_t kC16 = 1u << 16;
+
+    __shared__ long long s_tree;
+    __shared__ int s_cnt, s_err, s_qn, s_qh;
+    __shared__ unsigned long long s_draws;
+    __shared__ unsigned long long cyc[8];
+    __shared__ long long tmark;
+    if (tid < 8) cyc[tid] = 0ull;
+#define UST_PHASE(k)                                      \
+    do {                                                  \
+        if (tid == 0) {                                   \
+            const long long _now = clock64();             \
+            cyc[k] += (unsigned long long)(_now - tmark); \
+            tmark = _now;                                 \
+        }                                                 \
+    } while (0)
+
+    unsigned long long my_draws = 0, my_rounds = 0;
+    int my_max_rounds = 0, my_max_pops = 0;
+    const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
+
+    for (;;) {
+        if (tid == 0) s_tree = p.t_begin + (long long)atomicAdd(p.next_tree, 1ull);
+        __syncthreads();
+        const long long t = s_tree;
+        if (t >= p.t_end) break;
+        const uint32_t tree = (uint32_t)t;
+        if (tid == 0) tmark = clock64();
+
+        // ---- 1. cycle popping --------------------------------------------
+        for (int w = tid; w < nhalf; w += BT) lo32[w] = 0u;
+        for (int v = tid; v < n; v += BT) {
+            pop[v] = 0;
+            const int y = (v == u) ? -1 : stack_entry(p, v, 0u, tree);
+            nxt[v] = y;
+            nx16[v] = (uint16_t)y;
+        }
+        if (tid == 0) {
+            s_draws = (unsigned long long)(n - 1);
+            s_cnt = 0;
+            s_err = 0;
+            s_qn = 0;
+            s_qh = 0;
+        }
+        __syncthreads();
+        UST_PHASE(0);
+        for (int v = tid; v < n; v += BT)
+            if (v != u) half_add(lo32, nx16[v], 1);  // in-degrees
+        __syncthreads();
+        UST_PHASE(1);
+        // round 0: peel from the leaves (queued before any count moves);
+        // every thread keeps kWalks walks in flight.
+        {
+            int32_t *Q = L0;
+            for (int it = 0; it < iters; ++it) {
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int v = tid + (it * kWalks + k) * BT;
+                    const bool leaf = v < n && v != u && lo16[v] == 0;
+                    const int y0 = leaf ? (int)nx16[v] : u;
+                    warp_append(leaf && y0 != u, y0, Q, &s_qn);
+                }
+            }
+            __syncthreads();
+            const int qn = s_qn;
+            int idx = atomicAdd(&s_qh, 1);
+            int spare = (idx < qn) ? Q[idx] : u;
+            int y[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                y[k] = spare;
+                idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
+                spare = (idx < qn) ? Q[idx] : u;
+            }
+            for (int guard = 0; guard <= 2 * n + 2; ++guard) {
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    if (y[k] != u && half_add(lo32, y[k], -1) == 1u) {
+                        y[k] = nx16[y[k]];  // y peeled: remove its out-edge next
+                    } else {
+                        y[k] = spare;
+                        idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
+                        spare = (idx < qn) ? Q[idx] : u;
+                    }
+                    any |= (y[k] != u);
+                }
+                if (!any) break;
+            }
+        }
+        __syncthreads();
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = tid + (it * kWalks + k) * BT;
+                const bool cyc_v = v < n && v != u && lo16[v] != 0;  // still has an in-edge: on a cycle
+                warp_append(cyc_v, v, XA, &s_cnt);
+            }
+        }
+        __syncthreads();
+        for (int v = tid; v < n; v += BT) lo16[v] = (v == u) ? kFinal16 : 0;  // round marks
+        __syncthreads();
+        UST_PHASE(2);
+        int nX = s_cnt;
+
+        int rounds = 0;
+        bool failed = false;
+        int32_t *X = XA, *Xn = XB;
+        while (nX > 0) {
+            ++rounds;
+            if (rounds > p.max_rounds) {
+                failed = true;
+                if (tid == 0) atomicOr(p.status, kStatusPopRounds);
+                break;
+            }
+            const int stamp = (rounds - 1) % kMaxStamp16 + 1;
+            if (stamp == 1 && rounds > 1) {  // stamps wrap: forget old ones
+                for (int v = tid; v < n; v += BT)
+                    if (lo16[v] != kFinal16) lo16[v] = 0;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_draws += (unsigned long long)nX;
+                s_cnt = 0;
+                my_max_pops = max(my_max_pops, nX);
+            }
+            // (a) pop: every vertex on a cycle advances to its next stack entry
+            for (int i = tid; i < nX; i += BT) {
+                const int x = X[i];
+                const int k = pop[x] + 1;
+                const int y = stack_entry(p, x, (uint32_t)k, tree);
+                pop[x] = k;
+                nxt[x] = y;
+                nx16[x] = (uint16_t)y;
+                lo16[x] = (uint16_t)stamp;
+                pos[x] = i;
+            }
+            __syncthreads();
+            // (b) S(x): first redrawn vertex or known-final vertex after x
+            for (int i = tid; i < nX; i += BT) {
+                int y = nx16[X[i]];
+                int res = -2;
+                for (int guard = 0; guard <= n; ++guard) {
+                    const int m = lo16[y];
+                    if (m == kFinal16) { res = -1; break; }
+                    if (m == stamp) { res = pos[y]; break; }
+                    y = nx16[y];
+                }
+                if (res == -2) { s_err = 1; res = -1; }
+                Sx[i] = res;
+                J0[i] = res;
+                L0[i] = (res < 0) ? -1 : i;
+            }
+            __syncthreads();
+            // (c) min-label pointer jumping on the graph i -> S(i); -1 absorbs
+            int32_t *Jc = J0, *Lc = L0, *Jn = J1, *Ln = L1;
+            bool converged = false;
+            for (int step = 0; step < p.max_steps; ++step) {
+                int changed = 0;
+                for (int i = tid; i < nX; i += BT) {
+                    const int j = Jc[i];
+                    const int li = Lc[i];
+                    int nj, nl;
+                    if (j < 0) {
+                        nj = -1;
+                        nl = -1;
+                    } else {
+                        nj = Jc[j];
+                        nl = min(li, Lc[j]);
+                    }
+                    Jn[i] = nj;
+                    Ln[i] = nl;
+                    changed |= (nl != li);
+                }
+                int32_t *tmp;
+                tmp = Jc; Jc = Jn; Jn = tmp;
+                tmp = Lc; Lc = Ln; Ln = tmp;
+                if (!__syncthreads_or(changed)) {
+                    converged = true;
+                    break;
+                }
+            }
+            if (!converged) {
+                failed = true;
+                if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
+                break;
+            }
+            // (d) segments that reach u become final; the smallest node of
+            //     each cycle of i -> S(i) flags the cycle (pos[x] = -1)
+            for (int i = tid; i < nX; i += BT) {
+                const int li = Lc[i];
+                if (li == -1) {
+                    int y = X[i];
+                    for (int guard = 0; guard <= n; ++guard) {
+                        lo16[y] = kFinal16;
+                        y = nx16[y];
+                        const int m = lo16[y];
+                        if (m == kFinal16 || m == stamp) break;
+                    }
+                } else if (li == i) {
+                    int j = Sx[i], len = 1;
+                    while (j != i && j >= 0 && Lc[j] == i && len <= nX) {
+                        j = Sx[j];
+                        ++len;
+                    }
+                    if (j == i) {
+                        do {
+                            pos[X[j]] = -1;
+                            j = Sx[j];
+                        } while (j != i);
+                    }
+                }
+            }
+            __syncthreads();
+            // (e) the vertex cycles: each flagged x with its segment up to S(x)
+            for (int i = tid; i < nX; i += BT) {
+                int y = X[i];
+                if (pos[y] != -1) continue;
+                for (int guard = 0; guard <= n; ++guard) {
+                    Xn[atomicAdd(&s_cnt, 1)] = y;
+                    y = nx16[y];
+                    if (lo16[y] == stamp) break;
+                }
+            }
+            __syncthreads();
+            nX = s_cnt;
+            int32_t *tmp = X; X = Xn; Xn = tmp;
+            if (s_err) {
+                failed = true;
+                if (tid == 0) atomicOr(p.status, kStatusBadState);
+                break;
+            }
+        }
+        if (failed) break;
+        UST_PHASE(3);
+        if (tid == 0) {
+            my_draws += s_draws;
+            my_rounds += (unsigned long long)rounds;
+            my_max_rounds = max(my_max_rounds, rounds);
+        }
+
+        if (p.mode == 1) {
+            const long long o = (t - p.t_begin) * (long long)n;
+            for (int v = tid; v < n; v += BT) {
+                p.next_out[o + v] = nxt[v];
+                if (p.pops_out) p.pops_out[o + v] = pop[v];
+            }
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();
+
+        // ---- 2. DFS intervals ---------------------------------------------
+        // Subtree sizes from the leaves: C[v] = pending children << 16 | sum
+        // of finished children's sizes (0 exactly for leaves); the last child
+        // continues upwards and each arrival reads its offset inside the
+        // parent's interval from the same atomic.
+        for (int v = tid; v < n; v += BT) C[v] = 0u;
+        if (tid == 0) {
+            s_qn = 0;
+            s_qh = 0;
+        }
+        __syncthreads();
+        for (int v = tid; v < n; v += BT)
+            if (v != u) atomicAdd(&C[nxt[v]], kC16);
+        __syncthreads();
+        {
+            for (int it = 0; it < iters; ++it) {
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    const int v = tid + (it * kWalks + k) * BT;
+                    const bool leaf = v < n && v != u && C[v] == 0u;
+                    const unsigned m = __ballot_sync(0xffffffffu, leaf);
+                    const unsigned lane = threadIdx.x & 31u;
+                    int b = 0;
+                    if (lane == 0 && m) b = atomicAdd(&s_qn, __popc(m));
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    if (leaf)
+                        Q2[b + __popc(m & ((1u << lane) - 1u))] =
+                            ((unsigned long long)(uint32_t)v << 32) | (uint32_t)nxt[v];
+                }
+            }
+            __syncthreads();
+            const int qn = s_qn;
+            const unsigned long long kNone = ~0ull;
+            int idx = atomicAdd(&s_qh, 1);
+            unsigned long long spare = (idx < qn) ? Q2[idx] : kNone;
+            int x[kWalks], par[kWalks];
+            uint32_t carry[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
+                par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
+                carry[k] = 1u;
+                idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
+                spare = (idx < qn) ? Q2[idx] : kNone;
+            }
+            for (int guard = 0; guard <= 2 * n + 2; ++guard) {
+                uint32_t old[kWalks];
+                int gp[kWalks];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    old[k] = (par[k] >= 0) ? atomicAdd(&C[par[k]], carry[k] - kC16) : 0u;
+                    gp[k] = (par[k] >= 0 && par[k] != u) ? nxt[par[k]] : -1;
+                }
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+                    if (par[k] >= 0) {
+                        off[x[k]] = 1 + (int)(old[k] & 0xFFFFu);
+                        if (par[k] != u && (old[k] >> 16) == 1u) {
+                            carry[k] = (old[k] & 0xFFFFu) + carry[k] + 1u;
+                            x[k] = par[k];
+                            par[k] = gp[k];
+                        } else {
+                            x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
+                            par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
+                            carry[k] = 1u;
+                            idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
+                            spare = (idx < qn) ? Q2[idx] : kNone;
+                        }
+                    }
+                    any |= (par[k] >= 0);
+                }
+                if (!any) break;
+            }
+        }
+        __syncthreads();
+        UST_PHASE(4);
+        // preorder numbers: sizes go to global memory, then the shared words
+        // become (ancestor << 16 | partial offset sum) and pointer jumping
+        // sums the offsets up to u in place.
+        for (int v = tid; v < n; v += BT) {
+            gsz[v] = (int)(C[v] & 0xFFFFu) + 1;
+            C[v] = (v == u) ? ((uint32_t)u << 16) : (((uint32_t)nxt[v] << 16) | (uint32_t)off[v]);
+        }
+        __syncthreads();
+        bool jfail = true;
+        for (int step = 0; step < p.max_steps + 2; ++step) {
+            int pending = 0;
+            for (int v = tid; v < n; v += BT) {
+                const uint32_t a = C[v];
+                const int j = (int)(a >> 16);
+                if (j == u) continue;
+                const uint32_t b = C[j];
+                const int j2 = (int)(b >> 16);
+                C[v] = (b & 0xFFFF0000u) | ((a + b) & 0xFFFFu);
+                pending |= (j2 != u);
+            }
+            if (!__syncthreads_or(pending)) {
+                jfail = false;
+                break;
+            }
+        }
+        if (jfail) {
+            if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
+            break;
+        }
+        UST_PHASE(5);
+
+        // ---- 3. Algorithm 2 ------------------------------------------------
+        for (int v = tid; v < n; v += BT) {
+            if (v == u) continue;
+            const int pv = (int)(C[v] & 0xFFFFu);
+            const int s0 = __ldg(p.pathptr + v);
+            const int d = __ldg(p.pathptr + v + 1) - s0;
+            int prevb = v, prevnb = nxt[v];
+            int cnt = 0;
+            for (int c = 0; c < d; c += kPathChunk) {
+                int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(p.path + s0 + c + j) : -1;
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) {
+                    const int b = (j == 0) ? prevb : a[j - 1];
+                    const int nb = (j == 0) ? prevnb : na[j - 1];
+                    tx[j] = -1;
+                    sg[j] = 0;
+                    if (a[j] >= 0) {
+                        if (nb == a[j]) {
+                            tx[j] = b;
+                            sg[j] = 1;
+                        } else if (na[j] == b) {
+                            tx[j] = a[j];
+                            sg[j] = -1;
+                        }
+                    }
+                }
+                int lo[kPathChunk], sz[kPathChunk];
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j) {
+                    lo[j] = (sg[j] != 0) ? (int)(C[tx[j]] & 0xFFFFu) : 0;
+                    sz[j] = (sg[j] != 0) ? gsz[tx[j]] : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kPathChunk; ++j)
+                    if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
+                prevb = a[kPathChunk - 1];
+                prevnb = na[kPathChunk - 1];
+            }
+            Rp[v] += cnt;
+        }
+        __syncthreads();
+        UST_PHASE(6);
+        if (tid == 0) {
+            unsigned long long tot = 0ull;
+            for (int k = 0; k < 7; ++k) tot += cyc[k];
+            cyc[7] = tot;
+        }
+    }
+#undef UST_PHASE
+
+    if (tid == 0) {
+        atomicAdd(p.stats + 0, my_draws);
+        atomicAdd(p.stats + 1, my_rounds);
+        atomicMax(p.stats + 2, (unsigned long long)my_max_rounds);
+        atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
+        for (int k = 0; k < 8; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
+    }
+}
+
 // out[v] += sum over partial rows of Rp[c][v] (exact, fixed order).
 __global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict__ Rp, long long *__restrict__ out)
 {
@@ -681,11 +1149,11 @@ template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
     if (p.n <= kSmemMaxN) {
-        const size_t bytes = (size_t)p.n * sizeof(uint32_t);
-        cudaError_t e = cudaFuncSetAttribute(sample_aggregate_kernel<BT, true>,
+        const size_t bytes = (size_t)((p.n + 1) / 2) * 2 * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
-        sample_aggregate_kernel<BT, true><<<grid, BT, bytes, st>>>(p);
+        sample_aggregate_smem_kernel<BT><<<grid, BT, bytes, st>>>(p);
     } else {
         sample_aggregate_kernel<BT, false><<<grid, BT, 0, st>>>(p);
     }
