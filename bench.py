@@ -301,8 +301,9 @@ def main() -> None:
                            "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads"},
                 "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,
                                             "solve": statistics.mean(solve_ms)},
-                "sampler_cycles_per_tree": dict(zip(["first_draws", "in_degrees", "peeling", "pop_rounds",
-                                                     "sizes_offsets", "preorder", "aggregation", "tree_total"],
+                "sampler_cycles_per_tree": dict(zip(["first_draws", "in_degrees", "leaf_queue", "peeling",
+                                                     "cycle_list", "pop_rounds", "child_counts", "sizes_offsets",
+                                                     "preorder", "aggregation", "tree_total"],
                                                     [c / max(1, info["last_trees"]) for c in info["last_phase_cycles"]])),
                 "draws_per_tree": statistics.mean(draws) / T, "cg_iters": info["cg_iters"],
                 "cg_refinements": info["cg_refinements"], "cg_relres": info["cg_relres"],

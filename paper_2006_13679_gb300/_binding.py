@@ -47,7 +47,7 @@ class ust_info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("bfs_ms", ctypes.c_double), ("sample_ms", ctypes.c_double),
                 ("reduce_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("combine_ms", ctypes.c_double),
                 ("last_trees", ctypes.c_int64), ("last_draws", ctypes.c_int64),
-                ("last_phase_cycles", ctypes.c_int64 * 8)]
+                ("last_phase_cycles", ctypes.c_int64 * 12)]
 
     def as_dict(self) -> dict:
         out = {}

@@ -116,8 +116,8 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     if (cudaMalloc(&c->d_dist, (size_t)n * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "bfs dist");
     if (cudaMalloc(&c->d_flag, 64) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "flag");
     if (cudaMalloc(&c->d_pathptr, ((size_t)n + 1) * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "paths");
-    if (cudaMalloc(&c->d_stats, 16 * sizeof(int64_t)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "stats");
-    if (cudaMallocHost(&c->h_stats, 16 * sizeof(int64_t)) != cudaSuccess)
+    if (cudaMalloc(&c->d_stats, 32 * sizeof(int64_t)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "stats");
+    if (cudaMallocHost(&c->h_stats, 32 * sizeof(int64_t)) != cudaSuccess)
         return ust::fail(c, UST_ENOMEM, "pinned stats");
     if (cudaMalloc(&c->d_R, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
     if (cudaMalloc(&c->d_Rtmp, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
@@ -332,7 +332,7 @@ int ust_get_info(const ust_ctx *h, ust_info *out)
     out->kernel_launches = c->launches;
     out->last_trees = c->last_trees;
     out->last_draws = c->last_draws;
-    for (int k = 0; k < 8; ++k) out->last_phase_cycles[k] = c->last_phase_cycles[k];
+    for (int k = 0; k < 12; ++k) out->last_phase_cycles[k] = c->last_phase_cycles[k];
     double *ms[Ctx::kEvPhases] = {&out->bfs_ms, &out->sample_ms, &out->reduce_ms, &out->solve_ms, &out->combine_ms};
     for (int ph = 0; ph < Ctx::kEvPhases; ++ph) {
         if (!c->ev_used[ph]) continue;

@@ -79,7 +79,7 @@ struct Ctx {
     bool ev_used[kEvPhases] = {};
     int64_t launches = 0;
     int64_t last_trees = 0, last_draws = 0;
-    int64_t last_phase_cycles[8] = {};
+    int64_t last_phase_cycles[12] = {};
 
     // committed state
     int64_t trees = 0;

@@ -713,9 +713,9 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
     __shared__ long long s_tree;
     __shared__ int s_cnt, s_err, s_qn, s_qh;
     __shared__ unsigned long long s_draws;
-    __shared__ unsigned long long cyc[8];
+    __shared__ unsigned long long cyc[12];
     __shared__ long long tmark;
-    if (tid < 8) cyc[tid] = 0ull;
+    if (tid < 12) cyc[tid] = 0ull;
 #define UST_PHASE(k)                                      \
     do {                                                  \
         if (tid == 0) {                                   \
@@ -772,6 +772,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 }
             }
             __syncthreads();
+            UST_PHASE(2);
             const int qn = s_qn;
             int idx = atomicAdd(&s_qh, 1);
             int spare = (idx < qn) ? Q[idx] : u;
@@ -799,6 +800,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             }
         }
         __syncthreads();
+        UST_PHASE(3);
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
@@ -810,7 +812,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         __syncthreads();
         for (int v = tid; v < n; v += BT) lo16[v] = (v == u) ? kFinal16 : 0;  // round marks
         __syncthreads();
-        UST_PHASE(2);
+        UST_PHASE(4);
         int nX = s_cnt;
 
         int rounds = 0;
@@ -942,7 +944,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             }
         }
         if (failed) break;
-        UST_PHASE(3);
+        UST_PHASE(5);
         if (tid == 0) {
             my_draws += s_draws;
             my_rounds += (unsigned long long)rounds;
@@ -991,6 +993,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 }
             }
             __syncthreads();
+            UST_PHASE(6);
             const int qn = s_qn;
             const unsigned long long kNone = ~0ull;
             int idx = atomicAdd(&s_qh, 1);
@@ -1036,7 +1039,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             }
         }
         __syncthreads();
-        UST_PHASE(4);
+        UST_PHASE(7);
         // preorder numbers: sizes go to global memory, then the shared words
         // become (ancestor << 16 | partial offset sum) and pointer jumping
         // sums the offsets up to u in place.
@@ -1066,58 +1069,70 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
             break;
         }
-        UST_PHASE(5);
+        // the high half (now u everywhere) becomes the tree parent, so one
+        // shared word per vertex serves Algorithm 2
+        for (int v = tid; v < n; v += BT) C[v] = ((uint32_t)(uint16_t)nxt[v] << 16) | (C[v] & 0xFFFFu);
+        __syncthreads();
+        UST_PHASE(8);
 
         // ---- 3. Algorithm 2 ------------------------------------------------
+        // C[x] = parent(x) << 16 | pre(x); parent(u) reads as 0xFFFF.
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
-            const int pv = (int)(C[v] & 0xFFFFu);
+            const uint32_t cv = C[v];
+            const int pv = (int)(cv & 0xFFFFu);
             const int s0 = __ldg(p.pathptr + v);
             const int d = __ldg(p.pathptr + v + 1) - s0;
-            int prevb = v, prevnb = nxt[v];
+            int prevb = v, prevnb = (int)(cv >> 16), prevpre = pv;
             int cnt = 0;
             for (int c = 0; c < d; c += kPathChunk) {
-                int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
+                int a[kPathChunk], na[kPathChunk], pa[kPathChunk], tx[kPathChunk], sg[kPathChunk], lo[kPathChunk];
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(p.path + s0 + c + j) : -1;
 #pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
+                for (int j = 0; j < kPathChunk; ++j) {
+                    const uint32_t w = (a[j] >= 0) ? C[a[j]] : 0xFFFE0000u;
+                    na[j] = (int)(w >> 16);
+                    pa[j] = (int)(w & 0xFFFFu);
+                }
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j) {
                     const int b = (j == 0) ? prevb : a[j - 1];
                     const int nb = (j == 0) ? prevnb : na[j - 1];
+                    const int pb = (j == 0) ? prevpre : pa[j - 1];
                     tx[j] = -1;
                     sg[j] = 0;
+                    lo[j] = 0;
                     if (a[j] >= 0) {
-                        if (nb == a[j]) {
+                        if (nb == a[j]) {  // the tree uses (a, b) downwards: interval of b
                             tx[j] = b;
                             sg[j] = 1;
-                        } else if (na[j] == b) {
+                            lo[j] = pb;
+                        } else if (na[j] == b) {  // upwards: interval of a
                             tx[j] = a[j];
                             sg[j] = -1;
+                            lo[j] = pa[j];
                         }
                     }
                 }
-                int lo[kPathChunk], sz[kPathChunk];
+                int sz[kPathChunk];
 #pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) {
-                    lo[j] = (sg[j] != 0) ? (int)(C[tx[j]] & 0xFFFFu) : 0;
-                    sz[j] = (sg[j] != 0) ? gsz[tx[j]] : 0;
-                }
+                for (int j = 0; j < kPathChunk; ++j) sz[j] = (sg[j] != 0) ? gsz[tx[j]] : 0;
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j)
                     if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
                 prevb = a[kPathChunk - 1];
                 prevnb = na[kPathChunk - 1];
+                prevpre = pa[kPathChunk - 1];
             }
             Rp[v] += cnt;
         }
         __syncthreads();
-        UST_PHASE(6);
+        UST_PHASE(9);
         if (tid == 0) {
             unsigned long long tot = 0ull;
-            for (int k = 0; k < 7; ++k) tot += cyc[k];
-            cyc[7] = tot;
+            for (int k = 0; k < 10; ++k) tot += cyc[k];
+            cyc[10] = tot;
         }
     }
 #undef UST_PHASE
@@ -1127,7 +1142,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         atomicAdd(p.stats + 1, my_rounds);
         atomicMax(p.stats + 2, (unsigned long long)my_max_rounds);
         atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
-        for (int k = 0; k < 8; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
+        for (int k = 0; k < 11; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
     }
 }
 
@@ -1185,7 +1200,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     const int grid = (int)std::min<int64_t>(c->ctas, t1 - t0);
     if (mode == 0)
         UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
-    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 16 * sizeof(int64_t), c->stream));
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
 
     SampleParams p;
     p.n = c->n;
@@ -1241,7 +1256,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
     }
-    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 32 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
     const int status = (int)c->h_stats[5];
     if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
@@ -1249,7 +1264,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     if (status) return fail(c, UST_ECUDA, "sampler reported an inconsistent state");
     c->last_trees = t1 - t0;
     c->last_draws = c->h_stats[0];
-    for (int k = 0; k < 8; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
+    for (int k = 0; k < 12; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
     if (draws) *draws = c->h_stats[0];
     if (rounds) *rounds = c->h_stats[1];
     if (max_rounds) *max_rounds = (int)c->h_stats[2];
@@ -1283,7 +1298,7 @@ constexpr int kNoAllocCtas = 32;
 constexpr int kNoAllocThreads = 256;
 constexpr long long kNoAllocStride = ((kNoAllocMaxN + 2 + 31) / 32) * 32;
 // layout in int32 words: sampler workspace | partial counts | dist | bfs parent
-//                        | path offsets | paths | stats (16 x int64)
+//                        | path offsets | paths | stats (32 x int64)
 constexpr long long kNaWs = 0;
 constexpr long long kNaRp = kNaWs + (long long)kNoAllocCtas * kWsArrays * kNoAllocStride;
 constexpr long long kNaDist = kNaRp + (long long)kNoAllocCtas * kNoAllocMaxN;
@@ -1291,7 +1306,7 @@ constexpr long long kNaBpar = kNaDist + kNoAllocMaxN;
 constexpr long long kNaPathPtr = kNaBpar + kNoAllocMaxN;
 constexpr long long kNaPath = kNaPathPtr + ((kNoAllocMaxN + 1 + 31) / 32) * 32;
 constexpr long long kNaStats = kNaPath + kNoAllocMaxPath;
-constexpr long long kNaWords = kNaStats + 2 * 16;
+constexpr long long kNaWords = kNaStats + 2 * 32;
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNaWords];
 
@@ -1413,14 +1428,14 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
     int32_t *pathptr = base + kNaPathPtr, *path = base + kNaPath;
     unsigned long long *stats = reinterpret_cast<unsigned long long *>(base + kNaStats);
     // the previous call's contents stay in the array: clear what must start at zero
-    if (cudaMemsetAsync(stats, 0, 16 * sizeof(unsigned long long), st) != cudaSuccess) return UST_ECUDA;
+    if (cudaMemsetAsync(stats, 0, 32 * sizeof(unsigned long long), st) != cudaSuccess) return UST_ECUDA;
     if (cudaMemsetAsync(Rp, 0, (size_t)kNoAllocCtas * n * sizeof(int32_t), st) != cudaSuccess) return UST_ECUDA;
     if (cudaMemsetAsync(R_out, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess) return UST_ECUDA;
     int *status = reinterpret_cast<int *>(stats + 5);
     noalloc_prepare_kernel<<<1, kPrepThreads, 0, st>>>(n, pivot, row_ptr, col_idx, dist, bpar, pathptr, path,
                                                         kNoAllocMaxPath, status);
     if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
-    unsigned long long h_stats[16];
+    unsigned long long h_stats[32];
     if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess) return UST_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return UST_ECUDA;
     if (h_stats[5] & 1) return UST_ENOTCONNECTED;
