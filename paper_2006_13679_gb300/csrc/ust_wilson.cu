@@ -739,11 +739,31 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
 
         // ---- 1. cycle popping --------------------------------------------
         for (int w = tid; w < nhalf; w += BT) lo32[w] = 0u;
-        for (int v = tid; v < n; v += BT) {
-            pop[v] = 0;
-            const int y = (v == u) ? -1 : stack_entry(p, v, 0u, tree);
-            nxt[v] = y;
-            nx16[v] = (uint16_t)y;
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int rb[kWalks], deg[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                const bool ok = v < n && v != u;
+                rb[k] = ok ? __ldg(p.rp + v) : 0;
+                deg[k] = ok ? __ldg(p.rp + v + 1) - rb[k] : 0;
+            }
+            int y[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                const unsigned long long x = philox_x64((uint32_t)v, 0u, tree, p.graph, p.key0, p.key1);
+                y[k] = (deg[k] > 0) ? __ldg(p.ci + rb[k] + (int)__umul64hi(x, (unsigned long long)deg[k])) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                if (v < n) {
+                    pop[v] = 0;
+                    nxt[v] = y[k];
+                    nx16[v] = (uint16_t)y[k];
+                }
+            }
         }
         if (tid == 0) {
             s_draws = (unsigned long long)(n - 1);
@@ -758,30 +778,28 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             if (v != u) half_add(lo32, nx16[v], 1);  // in-degrees
         __syncthreads();
         UST_PHASE(1);
-        // round 0: peel from the leaves (queued before any count moves);
-        // every thread keeps kWalks walks in flight.
+        // round 0: peel. Leaves are marked 0xFFFF first (no in-edge, so no
+        // walk touches their count); a peeled vertex ends at count 0, so the
+        // two never mix. Every thread scans its own vertices for leaves and
+        // keeps kWalks walks in flight, all in shared memory.
+        for (int v = tid; v < n; v += BT)
+            if (v != u && lo16[v] == 0) half_add(lo32, v, 0xFFFF);
+        __syncthreads();
+        UST_PHASE(2);
         {
-            int32_t *Q = L0;
-            for (int it = 0; it < iters; ++it) {
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int v = tid + (it * kWalks + k) * BT;
-                    const bool leaf = v < n && v != u && lo16[v] == 0;
-                    const int y0 = leaf ? (int)nx16[v] : u;
-                    warp_append(leaf && y0 != u, y0, Q, &s_qn);
-                }
-            }
-            __syncthreads();
-            UST_PHASE(2);
-            const int qn = s_qn;
-            int idx = atomicAdd(&s_qh, 1);
-            int spare = (idx < qn) ? Q[idx] : u;
+            int cand = tid;
             int y[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
-                y[k] = spare;
-                idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
-                spare = (idx < qn) ? Q[idx] : u;
+                y[k] = u;
+                while (cand < n) {
+                    const int v = cand;
+                    cand += BT;
+                    if (v != u && lo16[v] == kFinal16) {
+                        y[k] = nx16[v];
+                        if (y[k] != u) break;
+                    }
+                }
             }
             for (int guard = 0; guard <= 2 * n + 2; ++guard) {
                 bool any = false;
@@ -790,9 +808,15 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                     if (y[k] != u && half_add(lo32, y[k], -1) == 1u) {
                         y[k] = nx16[y[k]];  // y peeled: remove its out-edge next
                     } else {
-                        y[k] = spare;
-                        idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
-                        spare = (idx < qn) ? Q[idx] : u;
+                        y[k] = u;
+                        while (cand < n) {
+                            const int v = cand;
+                            cand += BT;
+                            if (v != u && lo16[v] == kFinal16) {
+                                y[k] = nx16[v];
+                                if (y[k] != u) break;
+                            }
+                        }
                     }
                     any |= (y[k] != u);
                 }
@@ -805,7 +829,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = tid + (it * kWalks + k) * BT;
-                const bool cyc_v = v < n && v != u && lo16[v] != 0;  // still has an in-edge: on a cycle
+                const bool cyc_v = v < n && v != u && lo16[v] != 0 && lo16[v] != kFinal16;  // on a cycle
                 warp_append(cyc_v, v, XA, &s_cnt);
             }
         }
@@ -968,45 +992,52 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         // continues upwards and each arrival reads its offset inside the
         // parent's interval from the same atomic.
         for (int v = tid; v < n; v += BT) C[v] = 0u;
-        if (tid == 0) {
-            s_qn = 0;
-            s_qh = 0;
+        __syncthreads();
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int y[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                y[k] = (v < n && v != u) ? nxt[v] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k)
+                if (y[k] >= 0) atomicAdd(&C[y[k]], kC16);
         }
         __syncthreads();
-        for (int v = tid; v < n; v += BT)
-            if (v != u) atomicAdd(&C[nxt[v]], kC16);
-        __syncthreads();
+        UST_PHASE(6);
         {
-            for (int it = 0; it < iters; ++it) {
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int v = tid + (it * kWalks + k) * BT;
-                    const bool leaf = v < n && v != u && C[v] == 0u;
-                    const unsigned m = __ballot_sync(0xffffffffu, leaf);
-                    const unsigned lane = threadIdx.x & 31u;
-                    int b = 0;
-                    if (lane == 0 && m) b = atomicAdd(&s_qn, __popc(m));
-                    b = __shfl_sync(0xffffffffu, b, 0);
-                    if (leaf)
-                        Q2[b + __popc(m & ((1u << lane) - 1u))] =
-                            ((unsigned long long)(uint32_t)v << 32) | (uint32_t)nxt[v];
+            // own leaves (C[v] == 0; inner vertices never return to 0), with
+            // the next start and its parent fetched one step ahead
+            int cand = tid;
+            int sv = -1, spar = -1;
+            while (cand < n) {
+                const int v = cand;
+                cand += BT;
+                if (v != u && C[v] == 0u) {
+                    sv = v;
+                    spar = nxt[v];
+                    break;
                 }
             }
-            __syncthreads();
-            UST_PHASE(6);
-            const int qn = s_qn;
-            const unsigned long long kNone = ~0ull;
-            int idx = atomicAdd(&s_qh, 1);
-            unsigned long long spare = (idx < qn) ? Q2[idx] : kNone;
             int x[kWalks], par[kWalks];
             uint32_t carry[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
-                x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
-                par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
+                x[k] = sv;
+                par[k] = spar;
                 carry[k] = 1u;
-                idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
-                spare = (idx < qn) ? Q2[idx] : kNone;
+                sv = -1;
+                spar = -1;
+                while (cand < n) {
+                    const int v = cand;
+                    cand += BT;
+                    if (v != u && C[v] == 0u) {
+                        sv = v;
+                        spar = nxt[v];
+                        break;
+                    }
+                }
             }
             for (int guard = 0; guard <= 2 * n + 2; ++guard) {
                 uint32_t old[kWalks];
@@ -1026,11 +1057,20 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                             x[k] = par[k];
                             par[k] = gp[k];
                         } else {
-                            x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
-                            par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
+                            x[k] = sv;
+                            par[k] = spar;
                             carry[k] = 1u;
-                            idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
-                            spare = (idx < qn) ? Q2[idx] : kNone;
+                            sv = -1;
+                            spar = -1;
+                            while (cand < n) {
+                                const int v = cand;
+                                cand += BT;
+                                if (v != u && C[v] == 0u) {
+                                    sv = v;
+                                    spar = nxt[v];
+                                    break;
+                                }
+                            }
                         }
                     }
                     any |= (par[k] >= 0);
@@ -1043,9 +1083,23 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         // preorder numbers: sizes go to global memory, then the shared words
         // become (ancestor << 16 | partial offset sum) and pointer jumping
         // sums the offsets up to u in place.
-        for (int v = tid; v < n; v += BT) {
-            gsz[v] = (int)(C[v] & 0xFFFFu) + 1;
-            C[v] = (v == u) ? ((uint32_t)u << 16) : (((uint32_t)nxt[v] << 16) | (uint32_t)off[v]);
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int pa[kWalks], of[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                const bool ok = v < n && v != u;
+                pa[k] = ok ? nxt[v] : u;
+                of[k] = ok ? off[v] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                if (v < n) {
+                    gsz[v] = (int)(C[v] & 0xFFFFu) + 1;
+                    C[v] = ((uint32_t)pa[k] << 16) | (uint32_t)of[k];
+                }
+            }
         }
         __syncthreads();
         bool jfail = true;
@@ -1071,7 +1125,19 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         }
         // the high half (now u everywhere) becomes the tree parent, so one
         // shared word per vertex serves Algorithm 2
-        for (int v = tid; v < n; v += BT) C[v] = ((uint32_t)(uint16_t)nxt[v] << 16) | (C[v] & 0xFFFFu);
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int pa[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                pa[k] = (v < n) ? nxt[v] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                if (v < n) C[v] = ((uint32_t)(uint16_t)pa[k] << 16) | (C[v] & 0xFFFFu);
+            }
+        }
         __syncthreads();
         UST_PHASE(8);
 
