@@ -31,8 +31,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "USTs sampled+aggregated/sec and diag(L†) wall time on 1 GB300; % of L2/HBM roofline"
-WORKLOAD = "rmat16"
 SEED = 0
+# workload -> (description, oracle sample in trees for the CPU baseline; None = all)
+WORKLOADS = {
+    "rmat16": ("R-MAT scale 16, edge factor 16, (0.57,0.19,0.19,0.05), LCC, max-degree pivot, 4096 trees", None),
+    "grid48": ("48x48 4-neighbour grid, pivot (24,24), 1000 trees", None),
+    "hyperbolic20": ("random hyperbolic graph n=2^20, avg degree 20, exponent 3, T=0, LCC, max-degree pivot, "
+                     "tau(eps=0.3)", 256),
+    "rmat22": ("R-MAT scale 22, edge factor 16, LCC, max-degree pivot, tau(eps=0.3)", 96),
+}
 
 # Algorithmic bytes (what the method must touch, no cache effects):
 #   per Wilson draw: row_ptr pair 8 B + col_idx 4 B + successor write 4 B + stack depth 4 B
@@ -127,15 +134,25 @@ def gpu_index(local_rank: int) -> int:
     return local_rank
 
 
+def workload_trees(g, u, T, eps):
+    """Trees per step: the workload's fixed count, else tau(eps) of Algorithm 1."""
+    if T is not None:
+        return T
+    import oracle
+    ecc, _, _ = oracle.bfs(g, u)
+    return oracle.tau(ecc, g.m, eps, 1.0 / g.n, 0.3)
+
+
 def run_reference(args, rank: int, world: int) -> None:
     """The oracle (plain C, OpenMP over trees) on the host cores."""
     if rank != 0:
         return
     import oracle
     import synth
-    g, u, T, _ = synth.workload(WORKLOAD)
+    g, u, T0, eps = synth.workload(args.workload)
+    T = workload_trees(g, u, T0, eps)
     threads = oracle.max_threads()
-    sample = T
+    sample = min(T, WORKLOADS[args.workload][1] or T)
 
     def step():
         ecc, dist, par = oracle.bfs(g, u)
@@ -155,27 +172,29 @@ def run_reference(args, rank: int, world: int) -> None:
     line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{WORKLOAD}: n={g.n} m={g.m} pivot={u} trees={sample} seed={SEED}",
-                       "sample": f"full workload: BFS + {sample} trees + FP64 CG + combine per step"},
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; n={g.n} m={g.m} pivot={u} "
+                                   f"trees={T} seed={SEED}",
+                       "sample": f"BFS + {sample} of the {T} trees + FP64 CG + combine per step"},
             "cpu_baseline": {"value": value, "unit": "trees/s", "cores": threads, "kind": "oracle",
                              "sample": f"{sample} trees of the workload per step"},
             "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(g, u, T) -> dict:
+def cpu_baseline(g, u, T, sample) -> dict:
     import oracle
     threads = oracle.max_threads()
     ecc, dist, par = oracle.bfs(g, u)
-    oracle.sample_aggregate(g, u, par, 0, 64, SEED, threads=threads)  # warm
+    oracle.sample_aggregate(g, u, par, 0, min(16, sample), SEED, threads=threads)  # warm
     t0 = time.perf_counter()
     ecc, dist, par = oracle.bfs(g, u)
-    R, _ = oracle.sample_aggregate(g, u, par, 0, T, SEED, threads=threads)
+    R, _ = oracle.sample_aggregate(g, u, par, 0, sample, SEED, threads=threads)
     x, _, _, _ = oracle.cg(g, u, tol=1e-9)
-    oracle.combine(R, T, x, u)
+    oracle.combine(R, sample, x, u)
     sec = time.perf_counter() - t0
-    return {"value": T / sec, "unit": "trees/s", "cores": threads, "kind": "oracle",
-            "sample": f"one full step ({T} trees + BFS + FP64 CG + combine), OpenMP over trees", "seconds": sec}
+    what = "one full step" if sample == T else f"BFS + {sample} of the {T} trees"
+    return {"value": sample / sec, "unit": "trees/s", "cores": threads, "kind": "oracle",
+            "sample": f"{what} + FP64 CG + combine, OpenMP over trees", "seconds": sec}
 
 
 def main() -> None:
@@ -186,6 +205,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat16", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -209,7 +229,8 @@ def main() -> None:
         dist.init_process_group("nccl")
 
     pkg.build()
-    g, u, T, _ = synth.workload(WORKLOAD)
+    g, u, T0, eps = synth.workload(args.workload)
+    T = workload_trees(g, u, T0, eps)
     seed = SEED + rank
     stream = torch.cuda.Stream()
     rp_d = torch.from_numpy(g.row_ptr).cuda()
@@ -291,12 +312,12 @@ def main() -> None:
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(g, u, T)
+            cpu = cpu_baseline(g, u, T, min(T, WORKLOADS[args.workload][1] or T))
         line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": f"{WORKLOAD}: R-MAT scale 16, edge factor 16, LCC n={g.n} m={g.m}, "
-                                       f"max-degree pivot {u}, {T} trees per GPU, seed {SEED}+rank",
+                "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; n={g.n} m={g.m}, "
+                                       f"pivot {u}, {T} trees per GPU, seed {SEED}+rank",
                            "l2": "flushed between timed steps (256 MB write)",
                            "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads"},
                 "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,
