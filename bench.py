@@ -32,6 +32,11 @@ if ROOT not in sys.path:
 
 METRIC = "USTs sampled+aggregated/sec and diag(L†) wall time on 1 GB300; % of L2/HBM roofline"
 SEED = 0
+# DRAM bytes (read + write) of one sampler launch on the rmat16 workload, from the ncu capture
+# summarised in profiles/sample_aggregate_rmat16.md. Reported only while the kernel source is
+# the one the capture was taken on.
+TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "2a17e8705ca68e52fcd689477bbdce1dffe37d0c", "bytes": 1.841372e9 + 4.048805e9}
+
 # workload -> (description, oracle sample in trees for the CPU baseline; None = all)
 WORKLOADS = {
     "rmat16": ("R-MAT scale 16, edge factor 16, (0.57,0.19,0.19,0.05), LCC, max-degree pivot, 4096 trees", None),
@@ -290,8 +295,17 @@ def main() -> None:
     alg = algorithmic_bytes(int(statistics.mean(draws)), T, g.n, info["farness"])
     peak, peak_kind = peaks()
     achieved = alg / (kernel_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        import hashlib
+        src = os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", "ust_wilson.cu")
+        if (args.workload == TRAFFIC_CAPTURE["workload"]
+                and hashlib.sha1(open(src, "rb").read()).hexdigest() == TRAFFIC_CAPTURE["sha1"]):
+            traffic = TRAFFIC_CAPTURE["bytes"]
+    except OSError:
+        traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "sample_aggregate_kernel", "kernel_ms": kernel_ms,
+                "traffic": traffic, "kernel": "sample_aggregate_kernel", "kernel_ms": kernel_ms,
                 "algorithmic_bytes": alg, "peak_kind": peak_kind}
 
     # end to end through the public API with host buffers (validation included)
