@@ -103,6 +103,30 @@ __device__ __forceinline__ void warp_append(bool flag, int val, int32_t *q, int 
     if (flag) q[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
+// Classifies node i of the round's small graph i -> S(i) (S(i) = -1 when the
+// walk from x_i reached a vertex known to reach u): returns 1 when the path
+// from i ends at -1, 2 when i lies on a cycle, 0 when it runs into a cycle
+// that does not contain i. Brent's cycle detection: O(tail + cycle) reads.
+__device__ __forceinline__ int classify_node(const int32_t *Sx, int i, int limit)
+{
+    int power = 1, lam = 1;
+    int tortoise = i;
+    int hare = Sx[i];
+    for (int guard = 0; guard <= 4 * limit + 8; ++guard) {
+        if (hare < 0) return 1;
+        if (hare == i) return 2;
+        if (hare == tortoise) return 0;  // a cycle reached without passing i
+        if (power == lam) {
+            tortoise = hare;
+            power <<= 1;
+            lam = 0;
+        }
+        hare = Sx[hare];
+        ++lam;
+    }
+    return 0;
+}
+
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
 constexpr int kPathChunk = 4;
@@ -124,8 +148,8 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     int32_t *pos = base + 3 * S_;     // index of a redrawn vertex in the round's list
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // redrawn vertices of this / next round
     int32_t *Sx = base + 6 * S_;      // S(x) as an index into the round's list, -1 = reaches u
-    int32_t *J0 = base + 7 * S_, *J1 = base + 8 * S_;
-    int32_t *L0 = base + 9 * S_, *L1 = base + 10 * S_;
+    int32_t *J0 = base + 7 * S_;   // with base + 8 * S_: packed 64-bit words (queue, preorder)
+    int32_t *L0 = base + 9 * S_;   // leaf queue of the peeling
     // children bookkeeping: high word = children not yet finished (the
     // children count while sampling), low word = summed subtree sizes
     unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);
@@ -297,12 +321,6 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 if (tid == 0) atomicOr(p.status, kStatusPopRounds);
                 break;
             }
-            __syncthreads();
-            if (tid == 0) {
-                s_draws += (unsigned long long)nX;
-                s_cnt = 0;
-                my_max_pops = max(my_max_pops, nX);
-            }
             // (a) pop: every vertex on a cycle advances to its next stack entry
             for (int i = tid; i < nX; i += BT) {
                 const int x = X[i];
@@ -318,6 +336,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                     if (y != u) atomicAdd(&P[y], kChild);
                 }
             }
+            if (tid == 0) {
+                s_draws += (unsigned long long)nX;
+                s_cnt = 0;
+                my_max_pops = max(my_max_pops, nX);
+            }
             __syncthreads();
             // (b) S(x): first redrawn vertex or known-final vertex after x
             for (int i = tid; i < nX; i += BT) {
@@ -332,79 +355,26 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
-                J0[i] = res;
-                L0[i] = (res < 0) ? -1 : i;
             }
             __syncthreads();
-            // (c) min-label pointer jumping on the graph i -> S(i); -1 absorbs
-            int32_t *Jc = J0, *Lc = L0, *Jn = J1, *Ln = L1;
-            bool converged = false;
-            for (int step = 0; step < p.max_steps; ++step) {
-                int changed = 0;
-                for (int i = tid; i < nX; i += BT) {
-                    const int j = Jc[i];
-                    const int li = Lc[i];
-                    int nj, nl;
-                    if (j < 0) {
-                        nj = -1;
-                        nl = -1;
-                    } else {
-                        nj = Jc[j];
-                        nl = min(li, Lc[j]);
-                    }
-                    Jn[i] = nj;
-                    Ln[i] = nl;
-                    changed |= (nl != li);
-                }
-                int32_t *tmp;
-                tmp = Jc; Jc = Jn; Jn = tmp;
-                tmp = Lc; Lc = Ln; Ln = tmp;
-                if (!__syncthreads_or(changed)) {
-                    converged = true;
-                    break;
-                }
-            }
-            if (!converged) {
-                failed = true;
-                if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
-                break;
-            }
-            // (d) segments that reach u become final; the smallest node of
-            //     each cycle of i -> S(i) flags the cycle (pos[x] = -1)
+            // (c) nodes that reach -1 mark their segment final; nodes on a
+            //     cycle of i -> S(i) queue their segment for popping
             for (int i = tid; i < nX; i += BT) {
-                const int li = Lc[i];
-                if (li == -1) {
-                    int y = X[i];
+                const int kind = classify_node(Sx, i, nX);
+                int y = X[i];
+                if (kind == 1) {
                     for (int guard = 0; guard <= n; ++guard) {
                         rmark[y] = kFinal;
                         y = nxt[y];
                         const int m = rmark[y];
                         if (m == kFinal || m == rounds) break;
                     }
-                } else if (li == i) {
-                    int j = Sx[i], len = 1;
-                    while (j != i && j >= 0 && Lc[j] == i && len <= nX) {
-                        j = Sx[j];
-                        ++len;
+                } else if (kind == 2) {
+                    for (int guard = 0; guard <= n; ++guard) {
+                        Xn[atomicAdd(&s_cnt, 1)] = y;
+                        y = nxt[y];
+                        if (rmark[y] == rounds) break;
                     }
-                    if (j == i) {
-                        j = i;
-                        do {
-                            pos[X[j]] = -1;
-                            j = Sx[j];
-                        } while (j != i);
-                    }
-                }
-            }
-            __syncthreads();
-            // (e) the vertex cycles: each flagged x with its segment up to S(x)
-            for (int i = tid; i < nX; i += BT) {
-                int y = X[i];
-                if (pos[y] != -1) continue;
-                for (int guard = 0; guard <= n; ++guard) {
-                    Xn[atomicAdd(&s_cnt, 1)] = y;
-                    y = nxt[y];
-                    if (rmark[y] == rounds) break;
                 }
             }
             __syncthreads();
@@ -415,6 +385,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 if (tid == 0) atomicOr(p.status, kStatusBadState);
                 break;
             }
+            __syncthreads();
         }
         if (failed) break;
         UST_PHASE(3);
@@ -703,9 +674,6 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
     int32_t *pos = base + 3 * S_;     // index of a redrawn vertex in the round's list
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;
     int32_t *Sx = base + 6 * S_;
-    int32_t *J0 = base + 7 * S_, *J1 = base + 8 * S_;
-    int32_t *L0 = base + 9 * S_, *L1 = base + 10 * S_;
-    unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(base + 11 * S_);  // leaf queue
     int32_t *off = XA;
     int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
     constexpr uint32_t kC16 = 1u << 16;
@@ -853,12 +821,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             if (stamp == 1 && rounds > 1) {  // stamps wrap: forget old ones
                 for (int v = tid; v < n; v += BT)
                     if (lo16[v] != kFinal16) lo16[v] = 0;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                s_draws += (unsigned long long)nX;
-                s_cnt = 0;
-                my_max_pops = max(my_max_pops, nX);
+                __syncthreads();
             }
             // (a) pop: every vertex on a cycle advances to its next stack entry
             for (int i = tid; i < nX; i += BT) {
@@ -870,6 +833,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 nx16[x] = (uint16_t)y;
                 lo16[x] = (uint16_t)stamp;
                 pos[x] = i;
+            }
+            if (tid == 0) {
+                s_draws += (unsigned long long)nX;
+                s_cnt = 0;
+                my_max_pops = max(my_max_pops, nX);
             }
             __syncthreads();
             // (b) S(x): first redrawn vertex or known-final vertex after x
@@ -884,78 +852,27 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
-                J0[i] = res;
-                L0[i] = (res < 0) ? -1 : i;
             }
             __syncthreads();
-            // (c) min-label pointer jumping on the graph i -> S(i); -1 absorbs
-            int32_t *Jc = J0, *Lc = L0, *Jn = J1, *Ln = L1;
-            bool converged = false;
-            for (int step = 0; step < p.max_steps; ++step) {
-                int changed = 0;
-                for (int i = tid; i < nX; i += BT) {
-                    const int j = Jc[i];
-                    const int li = Lc[i];
-                    int nj, nl;
-                    if (j < 0) {
-                        nj = -1;
-                        nl = -1;
-                    } else {
-                        nj = Jc[j];
-                        nl = min(li, Lc[j]);
-                    }
-                    Jn[i] = nj;
-                    Ln[i] = nl;
-                    changed |= (nl != li);
-                }
-                int32_t *tmp;
-                tmp = Jc; Jc = Jn; Jn = tmp;
-                tmp = Lc; Lc = Ln; Ln = tmp;
-                if (!__syncthreads_or(changed)) {
-                    converged = true;
-                    break;
-                }
-            }
-            if (!converged) {
-                failed = true;
-                if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
-                break;
-            }
-            // (d) segments that reach u become final; the smallest node of
-            //     each cycle of i -> S(i) flags the cycle (pos[x] = -1)
+            // (c) nodes that reach -1 mark their segment final; nodes on a
+            //     cycle of i -> S(i) queue their segment (x up to S(x)) for
+            //     popping; the other nodes keep their stack tops.
             for (int i = tid; i < nX; i += BT) {
-                const int li = Lc[i];
-                if (li == -1) {
-                    int y = X[i];
+                const int kind = classify_node(Sx, i, nX);
+                int y = X[i];
+                if (kind == 1) {
                     for (int guard = 0; guard <= n; ++guard) {
                         lo16[y] = kFinal16;
                         y = nx16[y];
                         const int m = lo16[y];
                         if (m == kFinal16 || m == stamp) break;
                     }
-                } else if (li == i) {
-                    int j = Sx[i], len = 1;
-                    while (j != i && j >= 0 && Lc[j] == i && len <= nX) {
-                        j = Sx[j];
-                        ++len;
+                } else if (kind == 2) {
+                    for (int guard = 0; guard <= n; ++guard) {
+                        Xn[atomicAdd(&s_cnt, 1)] = y;
+                        y = nx16[y];
+                        if (lo16[y] == stamp) break;
                     }
-                    if (j == i) {
-                        do {
-                            pos[X[j]] = -1;
-                            j = Sx[j];
-                        } while (j != i);
-                    }
-                }
-            }
-            __syncthreads();
-            // (e) the vertex cycles: each flagged x with its segment up to S(x)
-            for (int i = tid; i < nX; i += BT) {
-                int y = X[i];
-                if (pos[y] != -1) continue;
-                for (int guard = 0; guard <= n; ++guard) {
-                    Xn[atomicAdd(&s_cnt, 1)] = y;
-                    y = nx16[y];
-                    if (lo16[y] == stamp) break;
                 }
             }
             __syncthreads();
@@ -966,6 +883,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 if (tid == 0) atomicOr(p.status, kStatusBadState);
                 break;
             }
+            __syncthreads();
         }
         if (failed) break;
         UST_PHASE(5);
