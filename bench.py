@@ -211,6 +211,8 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat16", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-comparator", action="store_true",
+                    help="skip the one-tree-per-launch + all-FP64-solve comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -323,6 +325,31 @@ def main() -> None:
     h2d = (g.n + 1) * 4 + g.nnz * 4
     d2h = g.n * 8
 
+    # In-GPU comparator: the same kernels launched for one tree at a time (one
+    # CTA per launch) and the column solved entirely in FP64 - the form the
+    # batched persistent launch and the mixed-precision solve replace. Timed
+    # once, on the same stream and events, outside the measured steps.
+    comparator = None
+    if not args.no_comparator and T <= 8192:
+        hc = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, solve_fp64=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hc.reset(u)
+        for _ in range(T):
+            hc.sample_aggregate(1, seed)
+        hc.diag(0.0, diag_d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1)
+        ci = hc.info()
+        comparator = {"form": "one tree per launch (1 CTA) + all-FP64 Jacobi-PCG column solve",
+                      "ms_per_step": cms, "value": T / (cms / 1e3), "unit": "trees/s",
+                      "solve_ms": ci["solve_ms"], "cg_iters": ci["cg_iters"],
+                      "batched_speedup": cms / ms}
+        hc.close()
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -346,7 +373,7 @@ def main() -> None:
                 "gpu_launches_per_step": launches / args.steps,
                 "e2e": ({"value": T / e2e_sec, "unit": "trees/s", "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": d2h, "ms_per_step": e2e_sec * 1e3} if e2e_sec else None),
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "comparator": comparator}
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:

@@ -93,6 +93,8 @@ typedef struct {
     int32_t graph_id;       /* fourth Philox counter word [0] */
     int32_t block_threads;  /* threads per sampling CTA, 0 = tuned default */
     int32_t ctas_per_sm;    /* sampling CTAs per SM, 0 = tuned default */
+    int32_t solve_fp64;     /* 1: run the whole column solve in FP64 (reference form) [0 = FP32 PCG
+                               inside FP64 refinement] */
     void *stream;           /* cudaStream_t to issue work on [NULL = legacy default stream] */
 } ust_opts;
 

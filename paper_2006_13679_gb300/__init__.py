@@ -62,7 +62,8 @@ class UST:
 
     def __init__(self, row_ptr, col_idx, pivot: int, *, delta: float = 0.0, kappa: float = 0.3,
                  cg_tol: float = 1e-9, max_pop_rounds: int = 0, max_cg_iters: int = 0, graph_id: int = 0,
-                 block_threads: int = 0, ctas_per_sm: int = 0, stream=None, skip_validation: bool = False):
+                 block_threads: int = 0, ctas_per_sm: int = 0, stream=None, skip_validation: bool = False,
+                 solve_fp64: bool = False):
         L = load()
         self._keep = []
         rp = row_ptr if _is_torch(row_ptr) else np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -79,6 +80,7 @@ class UST:
         o.max_pop_rounds, o.max_cg_iters = max_pop_rounds, max_cg_iters
         o.skip_validation = int(bool(skip_validation))
         o.graph_id, o.block_threads, o.ctas_per_sm = graph_id, block_threads, ctas_per_sm
+        o.solve_fp64 = int(bool(solve_fp64))
         sh = _stream_handle(stream)
         o.stream = sh.value if sh is not None else None
         h = ctypes.c_void_p()

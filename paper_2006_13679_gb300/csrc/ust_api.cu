@@ -43,6 +43,7 @@ void release(Ctx *c)
     cudaFree(c->d_f64);
     cudaFree(c->d_red);
     cudaFree(c->d_x);
+    cudaFree(c->d_f64inner);
     cudaFree(c->d_heavy);
     for (int i = 0; i < 2 * Ctx::kEvPhases; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -87,6 +88,7 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     c->max_pop_rounds = op.max_pop_rounds;  // 0: derived from the graph at each launch
     c->max_cg_iters = op.max_cg_iters > 0 ? op.max_cg_iters : 20000;
     c->graph_id = op.graph_id;
+    c->solve_fp64 = op.solve_fp64 != 0;
     c->stream = reinterpret_cast<cudaStream_t>(op.stream);
     UST_CUDA_TRY(cudaGetDevice(&c->device));
     for (int i = 0; i < 2 * Ctx::kEvPhases; ++i) UST_CUDA_TRY(cudaEventCreate(&c->ev[i]));

@@ -64,6 +64,8 @@ struct Ctx {
 
     // solve
     float *d_f32 = nullptr;     // inner PCG vectors
+    double *d_f64inner = nullptr;  // inner PCG vectors of the all-FP64 solve (allocated on first use)
+    bool solve_fp64 = false;
     double *d_f64 = nullptr;    // outer vectors
     double *d_red = nullptr;    // reduction partials
     double *h_red = nullptr;    // pinned scalars

@@ -120,11 +120,12 @@ __global__ void __launch_bounds__(kSolveThreads) residual_f64_kernel(int n, int 
 
 // Start of an inner solve: r32 = r64 - mean(r64), d = 0, z = r32 / deg,
 // p = z; partials of r.z.
+template <typename T>
 __global__ void __launch_bounds__(kSolveThreads) inner_start_kernel(int n, int nparts, const int32_t *__restrict__ rp,
                                                                     const double *__restrict__ r64,
                                                                     const double *__restrict__ part_in,
-                                                                    float *__restrict__ r, float *__restrict__ z,
-                                                                    float *__restrict__ p, float *__restrict__ d,
+                                                                    T *__restrict__ r, T *__restrict__ z,
+                                                                    T *__restrict__ p, T *__restrict__ d,
                                                                     double *part_out)
 {
     __shared__ double s_tmp[kSolveThreads / 32];
@@ -137,36 +138,37 @@ __global__ void __launch_bounds__(kSolveThreads) inner_start_kernel(int n, int n
     const double mean = s_mean;
     double rz = 0.0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const float rv = (float)(r64[v] - mean);
-        const float zv = rv / (float)(__ldg(rp + v + 1) - __ldg(rp + v));
+        const T rv = (T)(r64[v] - mean);
+        const T zv = rv / (T)(__ldg(rp + v + 1) - __ldg(rp + v));
         r[v] = rv;
         z[v] = zv;
         p[v] = zv;
-        d[v] = 0.0f;
+        d[v] = T(0);
         rz += (double)rv * (double)zv;
     }
     rz = block_sum(rz, s_tmp);
     if (threadIdx.x == 0) part_out[blockIdx.x] = rz;
 }
 
-// q = L p (FP32); partials of p.q.
-__global__ void __launch_bounds__(kSolveThreads) spmv_f32_kernel(int n, const int32_t *__restrict__ rp,
-                                                                 const int32_t *__restrict__ ci,
-                                                                 const int32_t *__restrict__ heavy, int nh,
-                                                                 const float *__restrict__ p, float *__restrict__ q,
-                                                                 double *part_out)
+// q = L p in the inner precision T; partials of p.q.
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) spmv_inner_kernel(int n, const int32_t *__restrict__ rp,
+                                                                   const int32_t *__restrict__ ci,
+                                                                   const int32_t *__restrict__ heavy, int nh,
+                                                                   const T *__restrict__ p, T *__restrict__ q,
+                                                                   double *part_out)
 {
     __shared__ double s_tmp[kSolveThreads / 32];
-    __shared__ float s_tmpf[kSolveThreads / 32];
+    __shared__ T s_tmpf[kSolveThreads / 32];
     if ((int)blockIdx.x < nh) {
         const int v = heavy[blockIdx.x];
         const int e0 = __ldg(rp + v), e1 = __ldg(rp + v + 1);
-        float s = 0.0f;
+        T s = T(0);
         for (int e = e0 + threadIdx.x; e < e1; e += kSolveThreads) s += p[__ldg(ci + e)];
         s = block_sum(s, s_tmpf);
         if (threadIdx.x == 0) {
-            const float pv = p[v];
-            const float qv = (float)(e1 - e0) * pv - s;
+            const T pv = p[v];
+            const T qv = (T)(e1 - e0) * pv - s;
             q[v] = qv;
             part_out[blockIdx.x] = (double)pv * (double)qv;
         }
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kSolveThreads) spmv_f32_kernel(int n, const in
     double pq = 0.0;
     for (int v0 = lb * rows_per_block; v0 < n; v0 += lgrid * rows_per_block) {
         const int v = v0 + threadIdx.x / kRowGroup;
-        float s = 0.0f;
+        T s = T(0);
         int e0 = 0, e1 = 0;
         if (v < n) {
             e0 = __ldg(rp + v);
@@ -189,8 +191,8 @@ __global__ void __launch_bounds__(kSolveThreads) spmv_f32_kernel(int n, const in
 #pragma unroll
         for (int o = kRowGroup / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, kRowGroup);
         if (v < n && g == 0 && e1 > e0) {
-            const float pv = p[v];
-            const float qv = (float)(e1 - e0) * pv - s;
+            const T pv = p[v];
+            const T qv = (T)(e1 - e0) * pv - s;
             q[v] = qv;
             pq += (double)pv * (double)qv;
         }
@@ -201,26 +203,27 @@ __global__ void __launch_bounds__(kSolveThreads) spmv_f32_kernel(int n, const in
 
 // alpha = rz / pq; d += alpha p; r -= alpha q; z = r / deg; partials of r.z
 // and r.r. rz of the current iteration is in sc[par].
+template <typename T>
 __global__ void __launch_bounds__(kSolveThreads) pcg_update_kernel(int n, int nparts, const int32_t *__restrict__ rp,
                                                                    const double *__restrict__ part_pq,
                                                                    const double *__restrict__ sc, int par,
-                                                                   float *__restrict__ d, float *__restrict__ r,
-                                                                   float *__restrict__ z, const float *__restrict__ p,
-                                                                   const float *__restrict__ q, double *part_out)
+                                                                   T *__restrict__ d, T *__restrict__ r,
+                                                                   T *__restrict__ z, const T *__restrict__ p,
+                                                                   const T *__restrict__ q, double *part_out)
 {
     __shared__ double s_tmp[kSolveThreads / 32];
-    __shared__ float s_alpha;
+    __shared__ T s_alpha;
     if (threadIdx.x < 32) {
         const double pq = warp_sum_partials(part_pq, nparts, 1);
-        if (threadIdx.x == 0) s_alpha = (pq > 0.0) ? (float)(sc[par] / pq) : 0.0f;
+        if (threadIdx.x == 0) s_alpha = (pq > 0.0) ? (T)(sc[par] / pq) : T(0);
     }
     __syncthreads();
-    const float alpha = s_alpha;
+    const T alpha = s_alpha;
     double rz = 0.0, rr = 0.0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         d[v] += alpha * p[v];
-        const float rv = r[v] - alpha * q[v];
-        const float zv = rv / (float)(__ldg(rp + v + 1) - __ldg(rp + v));
+        const T rv = r[v] - alpha * q[v];
+        const T zv = rv / (T)(__ldg(rp + v + 1) - __ldg(rp + v));
         r[v] = rv;
         z[v] = zv;
         rz += (double)rv * (double)zv;
@@ -235,21 +238,22 @@ __global__ void __launch_bounds__(kSolveThreads) pcg_update_kernel(int n, int np
 }
 
 // beta = rz_new / rz; p = z + beta p; block 0 stores rz_new in sc[par ^ 1].
+template <typename T>
 __global__ void __launch_bounds__(kSolveThreads) pcg_direction_kernel(int n, int nparts, const double *__restrict__ part_rz,
-                                                                      double *sc, int par, const float *__restrict__ z,
-                                                                      float *__restrict__ p)
+                                                                      double *sc, int par, const T *__restrict__ z,
+                                                                      T *__restrict__ p)
 {
-    __shared__ float s_beta;
+    __shared__ T s_beta;
     if (threadIdx.x < 32) {
         const double rz_new = warp_sum_partials(part_rz, nparts, 2);
         if (threadIdx.x == 0) {
             const double rz = sc[par];
-            s_beta = (rz > 0.0) ? (float)(rz_new / rz) : 0.0f;
+            s_beta = (rz > 0.0) ? (T)(rz_new / rz) : T(0);
             if (blockIdx.x == 0) sc[par ^ 1] = rz_new;
         }
     }
     __syncthreads();
-    const float beta = s_beta;
+    const T beta = s_beta;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) p[v] = z[v] + beta * p[v];
 }
 
@@ -261,7 +265,8 @@ __global__ void store_rz_kernel(int nparts, const double *__restrict__ part, dou
 }
 
 // x64 += d (FP64).
-__global__ void apply_correction_kernel(int n, const float *__restrict__ d, double *__restrict__ x)
+template <typename T>
+__global__ void apply_correction_kernel(int n, const T *__restrict__ d, double *__restrict__ x)
 {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) x[v] += (double)d[v];
 }
@@ -335,11 +340,17 @@ int alloc_solver(Ctx *c)
     return UST_OK;
 }
 
-int run_solve(Ctx *c)
+namespace {
+
+// One solve: FP64 residual and correction outside, Jacobi-PCG in T inside.
+// T = float is the mixed-precision default; T = double runs the whole CG in
+// FP64 (inner tolerance below cg_tol), the reference form of the solve.
+template <typename T>
+int solve_impl(Ctx *c, T *r, double inner_tol)
 {
-    const int n = c->n, nb = c->solve_blocks, nh = c->n_heavy, ns = nb + nh, T = kSolveThreads;
+    const int n = c->n, nb = c->solve_blocks, nh = c->n_heavy, ns = nb + nh, Tn = kSolveThreads;
     cudaStream_t st = c->stream;
-    float *r = c->d_f32, *z = r + n, *p = z + n, *q = p + n, *d = q + n;
+    T *z = r + n, *p = z + n, *q = p + n, *d = q + n;
     double *x = c->d_x, *r64 = c->d_f64;
     double *part_res = c->d_red;              // 2*ns
     double *part_a = part_res + 2 * ns;       // 2*ns
@@ -349,12 +360,11 @@ int run_solve(Ctx *c)
     UST_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), st));
 
     const double bnorm = sqrt(1.0 - 1.0 / (double)n);  // ||e_u - 1/n||_2
-    const double inner_tol = 1e-4;
     const int check_every = 8;
     int total_inner = 0, refinements = 0;
     double relres = 1.0;
     for (;;) {
-        residual_f64_kernel<<<ns, T, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
+        residual_f64_kernel<<<ns, Tn, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
         UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -365,7 +375,7 @@ int run_solve(Ctx *c)
         if (relres <= c->cg_tol) break;
         if (refinements >= 30) break;
         ++refinements;
-        inner_start_kernel<<<nb, T, 0, st>>>(n, ns, c->d_rp, r64, part_res, r, z, p, d, part_a);
+        inner_start_kernel<T><<<nb, Tn, 0, st>>>(n, ns, c->d_rp, r64, part_res, r, z, p, d, part_a);
         store_rz_kernel<<<1, 32, 0, st>>>(nb, part_a, sc);
         c->launches += 2;
         UST_CUDA_TRY(cudaGetLastError());
@@ -378,9 +388,9 @@ int run_solve(Ctx *c)
         bool inner_done = (rz0 <= 0.0);
         while (!inner_done && it < c->max_cg_iters) {
             for (int k = 0; k < check_every && it < c->max_cg_iters; ++k, ++it) {
-                spmv_f32_kernel<<<ns, T, 0, st>>>(n, c->d_rp, c->d_ci, c->d_heavy, nh, p, q, part_a);
-                pcg_update_kernel<<<nb, T, 0, st>>>(n, ns, c->d_rp, part_a, sc, par, d, r, z, p, q, part_b);
-                pcg_direction_kernel<<<nb, T, 0, st>>>(n, nb, part_b, sc, par, z, p);
+                spmv_inner_kernel<T><<<ns, Tn, 0, st>>>(n, c->d_rp, c->d_ci, c->d_heavy, nh, p, q, part_a);
+                pcg_update_kernel<T><<<nb, Tn, 0, st>>>(n, ns, c->d_rp, part_a, sc, par, d, r, z, p, q, part_b);
+                pcg_direction_kernel<T><<<nb, Tn, 0, st>>>(n, nb, part_b, sc, par, z, p);
                 c->launches += 3;
                 par ^= 1;
             }
@@ -392,16 +402,16 @@ int run_solve(Ctx *c)
             if (ri <= inner_tol * inner_tol * r0) inner_done = true;
         }
         total_inner += it;
-        apply_correction_kernel<<<nb, T, 0, st>>>(n, d, x);
+        apply_correction_kernel<T><<<nb, Tn, 0, st>>>(n, d, x);
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
     }
-    sum_kernel<<<nb, T, 0, st>>>(n, x, part_res);
-    project_kernel<<<nb, T, 0, st>>>(n, nb, part_res, x);
+    sum_kernel<<<nb, Tn, 0, st>>>(n, x, part_res);
+    project_kernel<<<nb, Tn, 0, st>>>(n, nb, part_res, x);
     c->launches += 2;
     UST_CUDA_TRY(cudaGetLastError());
     // residual of the projected solution
-    residual_f64_kernel<<<ns, T, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
+    residual_f64_kernel<<<ns, Tn, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
     c->launches += 1;
     phase_end(c, Ctx::kEvSolve);
     UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -415,6 +425,20 @@ int run_solve(Ctx *c)
     if (relres > c->cg_tol) return fail(c, UST_ENOTCONVERGED, "column solve did not reach cg_tol");
     c->x_valid = true;
     return UST_OK;
+}
+
+}  // namespace
+
+int run_solve(Ctx *c)
+{
+    if (c->solve_fp64) {
+        if (!c->d_f64inner) {
+            if (cudaMalloc(&c->d_f64inner, 5 * (size_t)c->n * sizeof(double)) != cudaSuccess)
+                return fail(c, UST_ENOMEM, "FP64 solver vectors");
+        }
+        return solve_impl<double>(c, c->d_f64inner, 0.25 * c->cg_tol);
+    }
+    return solve_impl<float>(c, c->d_f32, 1e-4);
 }
 
 int run_combine(Ctx *c, int64_t tau, double *d_diag)

@@ -39,8 +39,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_binding_structs_match_header_layout(lib):
     from paper_2006_13679_gb300 import _binding
-    # ust_opts: 3 doubles, 6 int32, pointer -> 3*8 + 6*4 + 8 = 56 bytes
-    assert ctypes.sizeof(_binding.ust_opts) == 56
+    # ust_opts: 3 doubles, 7 int32 (+4 padding), pointer -> 3*8 + 7*4 + 4 + 8 = 64 bytes
+    assert ctypes.sizeof(_binding.ust_opts) == 64
     assert ctypes.sizeof(_binding.ust_csr) == 32  # 2 int32, 2 pointers, int32 + padding
     o = _binding.default_opts()
     assert o.kappa == 0.3 and o.cg_tol == 1e-9 and o.skip_validation == 0
@@ -68,3 +68,25 @@ def test_product_package_does_not_import_the_oracle():
     csrc = os.path.join(ROOT, "paper_2006_13679_gb300", "csrc")
     for f in os.listdir(csrc):
         assert "orc_" not in open(os.path.join(csrc, f)).read(), f
+
+
+def test_struct_layout_matches_a_c_compiler(tmp_path):
+    """sizeof/offsetof of the ABI structs as gcc sees include/ust.h."""
+    import shutil
+    import subprocess
+    from paper_2006_13679_gb300 import _binding
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "ust.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(ust_csr), sizeof(ust_opts), sizeof(ust_info),'
+        ' offsetof(ust_opts, stream), offsetof(ust_info, cg_relres), offsetof(ust_info, last_phase_cycles));'
+        'return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(_binding.ust_csr), ctypes.sizeof(_binding.ust_opts), ctypes.sizeof(_binding.ust_info),
+            _binding.ust_opts.stream.offset, _binding.ust_info.cg_relres.offset,
+            _binding.ust_info.last_phase_cycles.offset]
+    assert got == want

@@ -256,3 +256,23 @@ def test_counts_above_shared_memory_limit(pkg, orc, maker):
         for i in range(3):
             ref, ref_pops, _ = orc.wilson(g, u, 100 + i, 21)
             assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
+
+
+def test_all_fp64_solve_matches(pkg, orc):
+    """The all-FP64 form of the column solve (the reference form the mixed
+    precision solve is compared with) reaches the same column."""
+    g, u, T, _ = synth.workload("rmat16")
+    with make(pkg, g, u, solve_fp64=True) as h:
+        x = h.column()
+        x_ref, _, _, ok = orc.cg(g, u, tol=1e-13)
+        assert ok and h.info()["cg_relres"] <= 1e-9
+        assert np.max(np.abs(x - x_ref)) <= COL_TOL * max(1.0, np.max(np.abs(x_ref)))
+
+
+def test_one_tree_per_launch_equals_batched(pkg, orc):
+    g, u = GRAPHS["rmat12"]()
+    with make(pkg, g, u) as a, make(pkg, g, u) as b:
+        a.sample_aggregate(64, 5)
+        for _ in range(64):
+            b.sample_aggregate(1, 5)
+        assert np.array_equal(a.counts(), b.counts())
