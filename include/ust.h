@@ -143,10 +143,35 @@ UST_API void ust_default_opts(ust_opts *o);
  * UST_ECUDA. On error *out is NULL. */
 UST_API int ust_init(const ust_csr *g, int32_t pivot, const ust_opts *o, ust_ctx **out);
 
+/* Creates a context for a batch of `count` graphs gs[0..count), graph g with
+ * pivot pivots[g] (Algorithm 1 for every graph at once). The graphs'
+ * vertices are laid out one after another: every per-vertex output (counts,
+ * columns, diagonals, B_u) holds graph 0's n_0 values, then graph 1's, and
+ * so on (ust_batch_offsets gives the offsets). Graph g draws its stacks with
+ * fourth Philox counter word graph_id + g. ust_sample_aggregate samples
+ * n_trees trees of every graph; ust_diag(eps > 0) tops every graph up to its
+ * own tau(eps); ust_tau returns the largest tau over the graphs;
+ * ust_reset(c, -1) recomputes every graph's B_u with its own pivot and clears
+ * all counts and columns. ust_tree_range_counts and ust_sample_trees apply to
+ * single-graph contexts only (UST_EINVAL). Errors as ust_init; the message
+ * names the graph. */
+UST_API int ust_init_batch(const ust_csr *gs, const int32_t *pivots, int32_t count, const ust_opts *o,
+                           ust_ctx **out);
+
+/* Number of graphs of a batch context, 0 for a single-graph context. */
+UST_API int32_t ust_batch_size(const ust_ctx *c);
+
+/* count+1 vertex offsets of a batch: graph g's values are at
+ * [offsets[g], offsets[g+1]) of every per-vertex output. */
+UST_API int ust_batch_offsets(const ust_ctx *c, int64_t *offsets_out);
+
+/* n, nnz, pivot, ecc, trees and f^c(u) of graph g of a batch. */
+UST_API int ust_batch_graph_info(const ust_ctx *c, int32_t g, ust_info *out);
+
 /* Re-targets the context to pivot u = pivot on the same graph: recomputes
  * B_u, ecc(u) and f^c(u) and clears R, the tree count and the cached column
- * (Algorithm 1 from its first line). No allocation. Errors: UST_EINVAL,
- * UST_ECUDA. */
+ * (Algorithm 1 from its first line). No allocation. A batch context keeps
+ * its pivots: pivot must be -1 there. Errors: UST_EINVAL, UST_ECUDA. */
 UST_API int ust_reset(ust_ctx *c, int32_t pivot);
 
 /* Samples trees with ids [trees, trees + n_trees) under `seed` and adds their

@@ -17,7 +17,7 @@ from ._binding import (UST_EINVAL, UST_ENOMEM, UST_ENOTCONNECTED, UST_ENOTCONVER
                        UST_ETIMEOUT, UST_OK, UstError, check, load)
 from ._build import LIB as LIB_PATH
 
-__all__ = ["UST", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
+__all__ = ["UST", "USTBatch", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
            "UST_ENOMEM", "UST_ETIMEOUT", "UST_ENOTCONVERGED", "UST_ESTATE"]
 
 
@@ -164,3 +164,73 @@ class UST:
         i = _binding.ust_info()
         check(load().ust_get_info(self._h, ctypes.byref(i)), self._h)
         return i.as_dict()
+
+
+class USTBatch:
+    """A batch of graphs in one context: ``ust_init_batch`` ... ``ust_free``.
+
+    graphs: list of (row_ptr, col_idx) int32 CSR arrays (numpy, host);
+    pivots: one pivot per graph. Per-vertex outputs are the graphs' values one
+    after another; ``offsets()`` gives where each graph starts. Graph g draws
+    with fourth Philox counter word graph_id + g.
+    """
+
+    def __init__(self, graphs, pivots, *, delta: float = 0.0, kappa: float = 0.3, cg_tol: float = 1e-9,
+                 max_pop_rounds: int = 0, max_cg_iters: int = 0, graph_id: int = 0, block_threads: int = 0,
+                 ctas_per_sm: int = 0, stream=None, skip_validation: bool = False, solve_fp64: bool = False):
+        L = load()
+        self._keep = []
+        csrs = (_binding.ust_csr * len(graphs))()
+        for i, (rp, ci) in enumerate(graphs):
+            rp = np.ascontiguousarray(rp, dtype=np.int32)
+            ci = np.ascontiguousarray(ci, dtype=np.int32)
+            self._keep += [rp, ci]
+            csrs[i] = _binding.ust_csr(n=int(rp.shape[0]) - 1, nnz=int(ci.shape[0]), row_ptr=rp.ctypes.data,
+                                       col_idx=ci.ctypes.data, on_device=0)
+        piv = np.ascontiguousarray(pivots, dtype=np.int32)
+        self._keep.append(piv)
+        o = _binding.default_opts()
+        o.delta, o.kappa, o.cg_tol = delta, kappa, cg_tol
+        o.max_pop_rounds, o.max_cg_iters = max_pop_rounds, max_cg_iters
+        o.skip_validation = int(bool(skip_validation))
+        o.graph_id, o.block_threads, o.ctas_per_sm = graph_id, block_threads, ctas_per_sm
+        o.solve_fp64 = int(bool(solve_fp64))
+        sh = _stream_handle(stream)
+        o.stream = sh.value if sh is not None else None
+        h = ctypes.c_void_p()
+        rc = L.ust_init_batch(csrs, piv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(graphs),
+                              ctypes.byref(o), ctypes.byref(h))
+        check(rc, None)
+        self._h = h
+        self.count = len(graphs)
+        self._off = np.empty(self.count + 1, dtype=np.int64)
+        check(L.ust_batch_offsets(h, ctypes.c_void_p(self._off.ctypes.data)), h)
+        self.n = int(self._off[-1])
+
+    def reset(self) -> None:
+        """Recomputes every graph's B_u (same pivots) and clears counts and columns."""
+        check(load().ust_reset(self._h, -1), self._h)
+
+    close = UST.close
+    __del__ = UST.__del__
+    __enter__ = UST.__enter__
+    __exit__ = UST.__exit__
+    sample_aggregate = UST.sample_aggregate
+    tau = UST.tau
+    _out = UST._out
+    diag = UST.diag
+    counts = UST.counts
+    column = UST.column
+    info = UST.info
+
+    def offsets(self) -> np.ndarray:
+        return self._off.copy()
+
+    def graph_info(self, g: int) -> dict:
+        i = _binding.ust_info()
+        check(load().ust_batch_graph_info(self._h, int(g), ctypes.byref(i)), self._h)
+        return i.as_dict()
+
+    def split(self, values) -> list:
+        """Per-graph views of a concatenated per-vertex output."""
+        return [values[self._off[g]:self._off[g + 1]] for g in range(self.count)]

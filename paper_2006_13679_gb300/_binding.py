@@ -62,6 +62,11 @@ _SIGNATURES = {
     "ust_default_opts": (None, [ctypes.POINTER(ust_opts)]),
     "ust_init": (ctypes.c_int, [ctypes.POINTER(ust_csr), ctypes.c_int32, ctypes.POINTER(ust_opts),
                                 ctypes.POINTER(ctypes.c_void_p)]),
+    "ust_init_batch": (ctypes.c_int, [ctypes.POINTER(ust_csr), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                      ctypes.POINTER(ust_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "ust_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "ust_batch_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ust_batch_graph_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ust_info)]),
     "ust_reset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "ust_sample_aggregate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]),
     "ust_diag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int32]),

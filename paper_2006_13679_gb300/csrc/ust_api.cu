@@ -45,11 +45,21 @@ void release(Ctx *c)
     cudaFree(c->d_x);
     cudaFree(c->d_f64inner);
     cudaFree(c->d_heavy);
+    cudaFree(c->d_graphs);
+    cudaFree(c->d_items);
+    cudaFree(c->d_comb);
+    cudaFree(c->d_prep);
+    cudaFree(c->d_prep_out);
+    cudaFreeHost(c->h_prep_out);
     for (int i = 0; i < 2 * Ctx::kEvPhases; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->h_red) cudaFreeHost(c->h_red);
 }
+
+}  // namespace
+
+namespace ust {
 
 // Host checks of the CSR contract: row_ptr monotone from 0 to nnz, columns
 // in range and strictly increasing per row, no self-loops, every arc present
@@ -73,6 +83,36 @@ int validate_csr(Ctx *c, int n, int nnz, const int32_t *rp, const int32_t *ci)
     return UST_OK;
 }
 
+int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, const ust_opts &op);
+int batch_sample_aggregate(Ctx *c, int64_t n_trees, uint64_t seed);
+int64_t batch_tau(const Ctx *c, double eps);
+int batch_diag(Ctx *c, double eps, double *diag_out, int32_t out_on_device);
+int batch_column(Ctx *c);
+int batch_reset(Ctx *c);
+
+}  // namespace ust
+
+namespace {
+
+using ust::validate_csr;
+
+// Context options shared by single graphs and batches.
+int apply_opts(Ctx *c, const ust_opts &op, int n)
+{
+    c->delta = op.delta > 0 ? op.delta : 1.0 / (double)n;
+    c->kappa = op.kappa > 0 ? op.kappa : 0.3;
+    c->cg_tol = op.cg_tol > 0 ? op.cg_tol : 1e-9;
+    c->max_pop_rounds = op.max_pop_rounds;
+    c->max_cg_iters = op.max_cg_iters > 0 ? op.max_cg_iters : 20000;
+    c->graph_id = op.graph_id;
+    c->solve_fp64 = op.solve_fp64 != 0;
+    c->stream = reinterpret_cast<cudaStream_t>(op.stream);
+    UST_CUDA_TRY(cudaGetDevice(&c->device));
+    for (int i = 0; i < 2 * Ctx::kEvPhases; ++i) UST_CUDA_TRY(cudaEventCreate(&c->ev[i]));
+    UST_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    return UST_OK;
+}
+
 int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
 {
     const int n = g->n, nnz = g->nnz;
@@ -82,17 +122,8 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     ust_opts def;
     ust_default_opts(&def);
     const ust_opts &op = o ? *o : def;
-    c->delta = op.delta > 0 ? op.delta : 1.0 / (double)n;
-    c->kappa = op.kappa > 0 ? op.kappa : 0.3;
-    c->cg_tol = op.cg_tol > 0 ? op.cg_tol : 1e-9;
-    c->max_pop_rounds = op.max_pop_rounds;  // 0: derived from the graph at each launch
-    c->max_cg_iters = op.max_cg_iters > 0 ? op.max_cg_iters : 20000;
-    c->graph_id = op.graph_id;
-    c->solve_fp64 = op.solve_fp64 != 0;
-    c->stream = reinterpret_cast<cudaStream_t>(op.stream);
-    UST_CUDA_TRY(cudaGetDevice(&c->device));
-    for (int i = 0; i < 2 * Ctx::kEvPhases; ++i) UST_CUDA_TRY(cudaEventCreate(&c->ev[i]));
-    UST_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int orc = apply_opts(c, op, n);
+    if (orc) return orc;
 
     if (!op.skip_validation) {
         std::vector<int32_t> hrp, hci;
@@ -121,6 +152,8 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     if (cudaMalloc(&c->d_stats, 32 * sizeof(int64_t)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "stats");
     if (cudaMallocHost(&c->h_stats, 32 * sizeof(int64_t)) != cudaSuccess)
         return ust::fail(c, UST_ENOMEM, "pinned stats");
+    if (cudaMalloc(&c->d_graphs, sizeof(ust::GraphDesc)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "descriptor");
+    if (cudaMalloc(&c->d_items, 2 * sizeof(long long)) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "items");
     if (cudaMalloc(&c->d_R, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
     if (cudaMalloc(&c->d_Rtmp, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)n * 8, c->stream));
@@ -177,10 +210,71 @@ int ust_init(const ust_csr *g, int32_t pivot, const ust_opts *o, ust_ctx **out)
     return UST_OK;
 }
 
+int ust_init_batch(const ust_csr *gs, const int32_t *pivots, int32_t count, const ust_opts *o, ust_ctx **out)
+{
+    if (!out) return UST_EINVAL;
+    *out = nullptr;
+    if (!gs || !pivots || count < 1) {
+        g_init_error = "invalid batch (need count >= 1 graphs and pivots)";
+        return UST_EINVAL;
+    }
+    ust_ctx *h = new (std::nothrow) ust_ctx;
+    if (!h) return UST_ENOMEM;
+    ust_opts def;
+    ust_default_opts(&def);
+    const ust_opts &op = o ? *o : def;
+    int rc = apply_opts(&h->c, op, gs[0].n > 0 ? gs[0].n : 2);
+    if (!rc) {
+        rc = ust::batch_init(&h->c, gs, pivots, count, op);
+        if (op.delta <= 0) h->c.delta = 0;  // per graph: 1 / n_g
+    }
+    if (rc) {
+        g_init_error = h->c.err;
+        release(&h->c);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return UST_OK;
+}
+
+int32_t ust_batch_size(const ust_ctx *h)
+{
+    return h ? h->c.batch : 0;
+}
+
+int ust_batch_offsets(const ust_ctx *h, int64_t *offsets_out)
+{
+    if (!h || !offsets_out || h->c.batch == 0) return UST_EINVAL;
+    for (int g = 0; g <= h->c.batch; ++g) offsets_out[g] = h->c.bvoff[g];
+    return UST_OK;
+}
+
+int ust_batch_graph_info(const ust_ctx *h, int32_t g, ust_info *out)
+{
+    if (!h || !out || g < 0 || g >= h->c.batch) return UST_EINVAL;
+    const Ctx *c = &h->c;
+    memset(out, 0, sizeof(*out));
+    out->n = c->bn[g];
+    out->nnz = c->bnnz[g];
+    out->pivot = c->bpivot[g];
+    out->ecc = c->becc[g];
+    out->trees = c->btrees[g];
+    out->seed = c->seed;
+    out->farness = c->bfarness[g];
+    out->sample_ctas = c->ctas;
+    out->sample_threads = c->block_threads;
+    return UST_OK;
+}
+
 int ust_reset(ust_ctx *h, int32_t pivot)
 {
     if (!h) return UST_EINVAL;
     Ctx *c = &h->c;
+    if (c->batch) {
+        if (pivot != -1) return ust::fail(c, UST_EINVAL, "a batch keeps its pivots: pass pivot = -1");
+        return ust::batch_reset(c);
+    }
     if (pivot < 0 || pivot >= c->n) return ust::fail(c, UST_EINVAL, "pivot out of range");
     c->pivot = pivot;
     c->trees = 0;
@@ -199,6 +293,7 @@ int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
     Ctx *c = &h->c;
     if (n_trees < 0) return ust::fail(c, UST_EINVAL, "n_trees < 0");
     if (n_trees == 0) return UST_OK;
+    if (c->batch) return ust::batch_sample_aggregate(c, n_trees, seed);
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_Rtmp, c->d_R, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
     int64_t draws = 0, rounds = 0;
     int max_rounds = 0, max_depth = 0;
@@ -219,6 +314,7 @@ int64_t ust_tau(const ust_ctx *h, double eps)
 {
     if (!h || !(eps > 0)) return 0;
     const Ctx *c = &h->c;
+    if (c->batch) return ust::batch_tau(c, eps);
     const double m = (double)c->nnz / 2.0;
     const double a = log(2.0 * m / c->delta);
     const double b = 2.0 * (1.0 - c->kappa) * (1.0 - c->kappa) * eps * eps;
@@ -230,6 +326,7 @@ int ust_diag(ust_ctx *h, double eps, double *diag_out, int32_t out_on_device)
     if (!h) return UST_EINVAL;
     Ctx *c = &h->c;
     if (!diag_out) return ust::fail(c, UST_EINVAL, "null output pointer");
+    if (c->batch) return ust::batch_diag(c, eps, diag_out, out_on_device);
     if (eps > 0) {
         const int64_t tau = ust_tau(h, eps);
         if (c->trees < tau) {
@@ -260,7 +357,7 @@ int ust_get_column(ust_ctx *h, double *x_out, int32_t out_on_device)
     if (!h) return UST_EINVAL;
     Ctx *c = &h->c;
     if (!c->x_valid) {
-        const int rc = ust::run_solve(c);
+        const int rc = c->batch ? ust::batch_column(c) : ust::run_solve(c);
         if (rc) return rc;
     }
     return copy_out(c, x_out, c->d_x, (size_t)c->n * 8, out_on_device);
@@ -283,6 +380,7 @@ int ust_tree_range_counts(ust_ctx *h, int64_t t0, int64_t t1, uint64_t seed, int
     if (!h) return UST_EINVAL;
     Ctx *c = &h->c;
     if (!R_out || t0 < 0 || t1 < t0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
+    if (c->batch) return ust::fail(c, UST_EINVAL, "ust_tree_range_counts applies to single-graph contexts");
     UST_CUDA_TRY(cudaMemsetAsync(c->d_Rtmp, 0, (size_t)c->n * 8, c->stream));
     const int rc = ust::run_sampler(c, t0, t1, seed, c->d_Rtmp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     if (rc) return rc;
@@ -294,6 +392,7 @@ int ust_sample_trees(ust_ctx *h, int64_t t0, int32_t count, uint64_t seed, int32
     if (!h) return UST_EINVAL;
     Ctx *c = &h->c;
     if (!next_out || count < 0 || t0 < 0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
+    if (c->batch) return ust::fail(c, UST_EINVAL, "ust_sample_trees applies to single-graph contexts");
     if (count == 0) return UST_OK;
     const size_t elems = (size_t)count * (size_t)c->n;
     int32_t *d_next = nullptr, *d_pops = nullptr;

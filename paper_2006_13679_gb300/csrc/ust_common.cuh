@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "ust.h"
 
@@ -26,11 +27,42 @@ enum : int {
     kStatusBadState = 4,   // an internal consistency check failed
 };
 
+// One graph of a launch: its CSR, pivot, B_u paths and where its trees and
+// counts go. A single-graph launch fills one from SampleParams; a batch
+// launch reads one per work item.
+struct GraphDesc {
+    int n, u;
+    uint32_t graph;            // fourth Philox counter word
+    long long voff;            // offset of the graph's vertices in batch-wide arrays
+    long long tree_begin;      // first tree id of the graph in this launch
+    const int32_t *rp, *ci, *bpar, *path, *pathptr;
+};
+
+// Graphs of at most this many vertices run the sampler with its per-tree
+// state in shared memory (4 bytes per vertex; ids below 2^16).
+constexpr int kSmemMaxVertices = 56 * 1024;
+
 // Per-CTA scratch of the sampling kernel: `kWsArrays` int32 arrays of
 // `stride` entries each, laid out array-major inside one CTA slot (the last
 // two form one 64-bit array).
+// Column solve: threads per CTA, and the row length above which one whole
+// CTA sums a row of the SpMV.
+constexpr int kSolveThreads = 256;
+constexpr int kHeavyRow = 256;
 constexpr int kWsArrays = 13;
 
+// One graph of a batched B_u launch (one CTA per graph).
+struct PrepDesc {
+    int n, u;
+    const int32_t *rp, *ci;
+    int32_t *dist, *bpar, *pathptr, *path;
+    long long path_cap;
+};
+// One graph of a batched diagonal combination.
+struct CombineDesc {
+    int n, u;
+    long long voff, trees;
+};
 struct Ctx {
     int n = 0;
     int nnz = 0;
@@ -65,6 +97,7 @@ struct Ctx {
     // solve
     float *d_f32 = nullptr;     // inner PCG vectors
     double *d_f64inner = nullptr;  // inner PCG vectors of the all-FP64 solve (allocated on first use)
+    int solve_n = 0;               // vertices the solver scratch is sized for
     bool solve_fp64 = false;
     double *d_f64 = nullptr;    // outer vectors
     double *d_red = nullptr;    // reduction partials
@@ -91,6 +124,21 @@ struct Ctx {
     int cg_iters = 0, cg_refinements = 0;
     double cg_relres = 0;
 
+    // batch of graphs (batch > 0): every per-vertex array holds the graphs'
+    // arrays one after another, graph g starting at bvoff[g]; row_ptr and
+    // pathptr hold n_g + 1 entries per graph, starting at bvoff[g] + g.
+    int batch = 0;
+    int ws_n = 0;  // vertices the sampler workspace is sized for (largest graph)
+    std::vector<int> bn, bnnz, bpivot, becc, bheavy_n, bblocks;
+    std::vector<int64_t> bvoff, baoff, bpoff, bhoff, btrees, bfarness;
+    GraphDesc *d_graphs = nullptr;  // sampler descriptors (one for a single graph)
+    GraphDesc single_desc{};        // last descriptor uploaded for a single graph
+    bool single_desc_valid = false;
+    long long *d_items = nullptr;
+    CombineDesc *d_comb = nullptr;
+    PrepDesc *d_prep = nullptr;
+    int32_t *d_prep_out = nullptr, *h_prep_out = nullptr;  // 3 x batch: status, ecc, f^c(u)
+
     std::string err;
 };
 
@@ -111,8 +159,23 @@ int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm);
 // mode 1: export next/pops of trees [t0, t1) to device buffers.
 int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
                 int32_t *d_pops_out, int64_t *draws, int64_t *rounds, int *max_rounds, int *max_depth);
+int run_batch_prepare(Ctx *c, const PrepDesc *d_desc, int count, int *d_out);
+int run_batch_combine(Ctx *c, const CombineDesc *d_desc, int count, double *d_diag);
+int run_batch_sampler(Ctx *c, const GraphDesc *d_graphs, const long long *d_item_start, int ngraphs,
+                      long long total_items, int max_n, long long max_rounds, uint64_t seed, int64_t *d_R,
+                      int64_t *draws, int64_t *rounds, int *max_round_count, int *max_pops);
+
+// One graph's column solve: the scratch vectors of the context are sized for
+// solve_n >= n vertices.
+struct SolveView {
+    int n = 0, u = 0;
+    const int32_t *rp = nullptr, *ci = nullptr, *heavy = nullptr;
+    int n_heavy = 0, blocks = 1;
+    double *x = nullptr;
+};
 int alloc_solver(Ctx *c);
 int run_solve(Ctx *c);
+int run_solve_view(Ctx *c, const SolveView &g);
 int run_combine(Ctx *c, int64_t tau, double *d_diag);
 
 }  // namespace ust

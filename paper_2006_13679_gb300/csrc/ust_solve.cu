@@ -22,7 +22,6 @@
 namespace ust {
 namespace {
 
-constexpr int kSolveThreads = 256;
 constexpr int kRowGroup = 8;  // lanes per CSR row in the SpMVs
 
 // Sum of `count` per-block partials at stride `stride`, identical in every
@@ -60,7 +59,6 @@ __device__ __forceinline__ T block_sum(T v, T *s_tmp)
 // Rows with more than kHeavyRow arcs are summed by a whole CTA each (the
 // first `nh` blocks of an SpMV launch); the other blocks give every light row
 // a group of kRowGroup lanes. Both reductions use a fixed order.
-constexpr int kHeavyRow = 256;
 
 // r64 = b - L x64; partials of sum(r) and sum(r^2).
 __global__ void __launch_bounds__(kSolveThreads) residual_f64_kernel(int n, int u, const int32_t *__restrict__ rp,
@@ -316,6 +314,7 @@ __global__ void combine_kernel(int n, int u, double tau, const long long *__rest
 int alloc_solver(Ctx *c)
 {
     const size_t n = (size_t)c->n;
+    c->solve_n = c->n;
     c->solve_blocks = std::max(1, std::min<int>(c->num_sms * 2, (int)((n + kSolveThreads - 1) / kSolveThreads)));
     // rows summed by a whole CTA in the SpMVs
     std::vector<int32_t> rp(n + 1), heavy;
@@ -346,12 +345,12 @@ namespace {
 // T = float is the mixed-precision default; T = double runs the whole CG in
 // FP64 (inner tolerance below cg_tol), the reference form of the solve.
 template <typename T>
-int solve_impl(Ctx *c, T *r, double inner_tol)
+int solve_impl(Ctx *c, const SolveView &g, T *r, double inner_tol)
 {
-    const int n = c->n, nb = c->solve_blocks, nh = c->n_heavy, ns = nb + nh, Tn = kSolveThreads;
+    const int n = g.n, nb = g.blocks, nh = g.n_heavy, ns = nb + nh, Tn = kSolveThreads;
     cudaStream_t st = c->stream;
     T *z = r + n, *p = z + n, *q = p + n, *d = q + n;
-    double *x = c->d_x, *r64 = c->d_f64;
+    double *x = g.x, *r64 = c->d_f64;
     double *part_res = c->d_red;              // 2*ns
     double *part_a = part_res + 2 * ns;       // 2*ns
     double *part_b = part_a + 2 * ns;         // 2*ns
@@ -364,7 +363,7 @@ int solve_impl(Ctx *c, T *r, double inner_tol)
     int total_inner = 0, refinements = 0;
     double relres = 1.0;
     for (;;) {
-        residual_f64_kernel<<<ns, Tn, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
+        residual_f64_kernel<<<ns, Tn, 0, st>>>(n, g.u, g.rp, g.ci, g.heavy, nh, x, r64, part_res);
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
         UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -375,7 +374,7 @@ int solve_impl(Ctx *c, T *r, double inner_tol)
         if (relres <= c->cg_tol) break;
         if (refinements >= 30) break;
         ++refinements;
-        inner_start_kernel<T><<<nb, Tn, 0, st>>>(n, ns, c->d_rp, r64, part_res, r, z, p, d, part_a);
+        inner_start_kernel<T><<<nb, Tn, 0, st>>>(n, ns, g.rp, r64, part_res, r, z, p, d, part_a);
         store_rz_kernel<<<1, 32, 0, st>>>(nb, part_a, sc);
         c->launches += 2;
         UST_CUDA_TRY(cudaGetLastError());
@@ -388,8 +387,8 @@ int solve_impl(Ctx *c, T *r, double inner_tol)
         bool inner_done = (rz0 <= 0.0);
         while (!inner_done && it < c->max_cg_iters) {
             for (int k = 0; k < check_every && it < c->max_cg_iters; ++k, ++it) {
-                spmv_inner_kernel<T><<<ns, Tn, 0, st>>>(n, c->d_rp, c->d_ci, c->d_heavy, nh, p, q, part_a);
-                pcg_update_kernel<T><<<nb, Tn, 0, st>>>(n, ns, c->d_rp, part_a, sc, par, d, r, z, p, q, part_b);
+                spmv_inner_kernel<T><<<ns, Tn, 0, st>>>(n, g.rp, g.ci, g.heavy, nh, p, q, part_a);
+                pcg_update_kernel<T><<<nb, Tn, 0, st>>>(n, ns, g.rp, part_a, sc, par, d, r, z, p, q, part_b);
                 pcg_direction_kernel<T><<<nb, Tn, 0, st>>>(n, nb, part_b, sc, par, z, p);
                 c->launches += 3;
                 par ^= 1;
@@ -411,7 +410,7 @@ int solve_impl(Ctx *c, T *r, double inner_tol)
     c->launches += 2;
     UST_CUDA_TRY(cudaGetLastError());
     // residual of the projected solution
-    residual_f64_kernel<<<ns, Tn, 0, st>>>(n, c->pivot, c->d_rp, c->d_ci, c->d_heavy, nh, x, r64, part_res);
+    residual_f64_kernel<<<ns, Tn, 0, st>>>(n, g.u, g.rp, g.ci, g.heavy, nh, x, r64, part_res);
     c->launches += 1;
     phase_end(c, Ctx::kEvSolve);
     UST_CUDA_TRY(cudaMemcpyAsync(c->h_red, part_res, 2 * ns * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -423,22 +422,37 @@ int solve_impl(Ctx *c, T *r, double inner_tol)
     c->cg_refinements = refinements;
     c->cg_relres = relres;
     if (relres > c->cg_tol) return fail(c, UST_ENOTCONVERGED, "column solve did not reach cg_tol");
-    c->x_valid = true;
     return UST_OK;
 }
 
 }  // namespace
 
-int run_solve(Ctx *c)
+int run_solve_view(Ctx *c, const SolveView &g)
 {
     if (c->solve_fp64) {
         if (!c->d_f64inner) {
-            if (cudaMalloc(&c->d_f64inner, 5 * (size_t)c->n * sizeof(double)) != cudaSuccess)
+            if (cudaMalloc(&c->d_f64inner, 5 * (size_t)c->solve_n * sizeof(double)) != cudaSuccess)
                 return fail(c, UST_ENOMEM, "FP64 solver vectors");
         }
-        return solve_impl<double>(c, c->d_f64inner, 0.25 * c->cg_tol);
+        return solve_impl<double>(c, g, c->d_f64inner, 0.25 * c->cg_tol);
     }
-    return solve_impl<float>(c, c->d_f32, 1e-4);
+    return solve_impl<float>(c, g, c->d_f32, 1e-4);
+}
+
+int run_solve(Ctx *c)
+{
+    SolveView g;
+    g.n = c->n;
+    g.u = c->pivot;
+    g.rp = c->d_rp;
+    g.ci = c->d_ci;
+    g.heavy = c->d_heavy;
+    g.n_heavy = c->n_heavy;
+    g.blocks = c->solve_blocks;
+    g.x = c->d_x;
+    const int rc = run_solve_view(c, g);
+    if (rc == UST_OK) c->x_valid = true;
+    return rc;
 }
 
 int run_combine(Ctx *c, int64_t tau, double *d_diag)

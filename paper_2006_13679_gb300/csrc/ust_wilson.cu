@@ -62,31 +62,56 @@ __device__ __forceinline__ unsigned long long philox_x64(uint32_t c0, uint32_t c
     return ((unsigned long long)c1 << 32) | (unsigned long long)c0;
 }
 
+// One launch of the sampler: work item i of [0, total_items) is tree
+// tree_offset + tree_begin + (i - item_start[g]) of graph graphs[g], where
+// item_start[g] <= i < item_start[g + 1]. A single graph is a one-entry
+// array; every launch reads its graphs from device memory.
 struct SampleParams {
-    int n, u;
-    uint32_t graph, key0, key1;
-    const int32_t *rp, *ci, *bpar;
-    const int32_t *path, *pathptr;  // ancestors of v on B_u, v's list at [pathptr[v], pathptr[v+1])
+    int max_n;  // largest graph of the launch: shared-memory and partial-count sizes
+    uint32_t key0, key1;
+    const GraphDesc *graphs;
+    int ngraphs;
+    const long long *item_start;
+    long long total_items;
+    long long tree_offset;
     int32_t *ws;
     long long stride;
-    int32_t *Rp;
-    long long t_begin, t_end;
+    int32_t *Rp;  // per-CTA partial counts (single graph), stride max_n
     unsigned long long *next_tree;
     unsigned long long *stats;  // [0] draws, [1] rounds, [2] max rounds, [3] max pops in one round
     int *status;
     int max_rounds, max_steps;
     int mode;  // 0: aggregate, 1: export trees
-    int32_t *next_out, *pops_out;
+    int32_t *next_out, *pops_out;  // mode 1: item i's tree at [i n, (i + 1) n)
+    unsigned long long *R_direct;   // when set, counts go to R_direct[voff + v] (batches)
 };
 
-// Stack entry `k` of vertex v: a uniformly chosen neighbour.
-__device__ __forceinline__ int stack_entry(const SampleParams &p, int v, uint32_t k, uint32_t tree)
+// item_start[1] of a one-graph launch: its items end at total_items.
+constexpr long long kOpenEnd = 1ll << 62;
+
+// The graph and tree id of a work item.
+__device__ __forceinline__ bool item_graph(const SampleParams &p, long long item, GraphDesc &gd, long long &t)
 {
-    const int b = __ldg(p.rp + v);
-    const int e = __ldg(p.rp + v + 1);
-    const unsigned long long x = philox_x64((uint32_t)v, k, tree, p.graph, p.key0, p.key1);
+    if (item >= p.total_items) return false;
+    int lo = 0, hi = p.ngraphs;  // item_start[lo] <= item < item_start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(p.item_start + mid) <= item) lo = mid; else hi = mid;
+    }
+    gd = p.graphs[lo];
+    t = p.tree_offset + gd.tree_begin + (item - __ldg(p.item_start + lo));
+    return true;
+}
+
+// Stack entry `k` of vertex v: a uniformly chosen neighbour.
+__device__ __forceinline__ int stack_entry(const GraphDesc &g, uint32_t key0, uint32_t key1, int v, uint32_t k,
+                                           uint32_t tree)
+{
+    const int b = __ldg(g.rp + v);
+    const int e = __ldg(g.rp + v + 1);
+    const unsigned long long x = philox_x64((uint32_t)v, k, tree, g.graph, key0, key1);
     const unsigned long long idx = __umul64hi(x, (unsigned long long)(e - b));
-    return __ldg(p.ci + b + (int)idx);
+    return __ldg(g.ci + b + (int)idx);
 }
 
 constexpr int kFinal = -1;  // mark of vertices known to reach u
@@ -139,7 +164,7 @@ template <int BT, bool SM>
 __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 {
     extern __shared__ uint32_t s_dyn[];
-    const int n = p.n, u = p.u, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
     int32_t *nxt = base;              // stack tops; the tree's parent array at the end
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     int32_t *rmark = SM ? reinterpret_cast<int32_t *>(s_dyn) : mark;  // marks of the popping rounds
     uint32_t *C = s_dyn;                                           // shared counters (SM only)
     constexpr uint32_t kC16 = 1u << 16;
-    int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
+    int32_t *Rp = p.Rp + (long long)blockIdx.x * p.max_n;
     constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
@@ -181,10 +206,12 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     int my_max_rounds = 0, my_max_pops = 0;
 
     for (;;) {
-        if (tid == 0) s_tree = p.t_begin + (long long)atomicAdd(p.next_tree, 1ull);
+        if (tid == 0) s_tree = (long long)atomicAdd(p.next_tree, 1ull);
         __syncthreads();
-        const long long t = s_tree;
-        if (t >= p.t_end) break;
+        GraphDesc gd;
+        long long t;
+        if (!item_graph(p, s_tree, gd, t)) break;
+        const int n = gd.n, u = gd.u;
         const uint32_t tree = (uint32_t)t;
         if (tid == 0) tmark = clock64();
 
@@ -197,7 +224,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 mark[v] = 0;
                 P[v] = 0ull;
             }
-            nxt[v] = (v == u) ? -1 : stack_entry(p, v, 0u, tree);
+            nxt[v] = (v == u) ? -1 : stack_entry(gd, p.key0, p.key1, v, 0u, tree);
         }
         if (tid == 0) {
             s_draws = (unsigned long long)(n - 1);
@@ -326,7 +353,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 const int x = X[i];
                 const int k = pop[x] + 1;
                 const int old = nxt[x];
-                const int y = stack_entry(p, x, (uint32_t)k, tree);
+                const int y = stack_entry(gd, p.key0, p.key1, x, (uint32_t)k, tree);
                 pop[x] = k;
                 nxt[x] = y;
                 rmark[x] = rounds;
@@ -396,7 +423,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         }
 
         if (p.mode == 1) {
-            const long long o = (t - p.t_begin) * (long long)n;
+            const long long o = s_tree * (long long)n;
             for (int v = tid; v < n; v += BT) {
                 p.next_out[o + v] = nxt[v];
                 if (p.pops_out) p.pops_out[o + v] = pop[v];
@@ -575,14 +602,14 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         for (int v = tid; v < n; v += BT) {
             if (v == u) continue;
             const int pv = (int)(uint32_t)JA[v];
-            const int s0 = __ldg(p.pathptr + v);
-            const int d = __ldg(p.pathptr + v + 1) - s0;
+            const int s0 = __ldg(gd.pathptr + v);
+            const int d = __ldg(gd.pathptr + v + 1) - s0;
             int prevb = v, prevnb = nxt[v];
             int cnt = 0;
             for (int c = 0; c < d; c += kPathChunk) {
                 int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
 #pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(p.path + s0 + c + j) : -1;
+                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
 #pragma unroll
@@ -613,7 +640,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
                 prevb = a[kPathChunk - 1];
                 prevnb = na[kPathChunk - 1];
             }
-            Rp[v] += cnt;
+            if (p.R_direct) {
+                if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
+            } else {
+                Rp[v] += cnt;
+            }
         }
         __syncthreads();
         UST_PHASE(6);
@@ -660,11 +691,9 @@ template <int BT>
 __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams p)
 {
     extern __shared__ uint32_t s_dyn[];
-    const int n = p.n, u = p.u, tid = threadIdx.x;
-    const int nhalf = (n + 1) >> 1;          // 32-bit words of one 16-bit array
+    const int tid = threadIdx.x;
     uint16_t *lo16 = reinterpret_cast<uint16_t *>(s_dyn);        // counts, then marks
     uint32_t *lo32 = s_dyn;                                      // the same, as words
-    uint16_t *nx16 = reinterpret_cast<uint16_t *>(s_dyn + nhalf);  // successors
     uint32_t *C = s_dyn;                                         // sizes / preorder words
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
@@ -675,7 +704,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;
     int32_t *Sx = base + 6 * S_;
     int32_t *off = XA;
-    int32_t *Rp = p.Rp + (long long)blockIdx.x * n;
+    int32_t *Rp = p.Rp + (long long)blockIdx.x * p.max_n;
     constexpr uint32_t kC16 = 1u << 16;
 
     __shared__ long long s_tree;
@@ -695,14 +724,18 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
 
     unsigned long long my_draws = 0, my_rounds = 0;
     int my_max_rounds = 0, my_max_pops = 0;
-    const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
 
     for (;;) {
-        if (tid == 0) s_tree = p.t_begin + (long long)atomicAdd(p.next_tree, 1ull);
+        if (tid == 0) s_tree = (long long)atomicAdd(p.next_tree, 1ull);
         __syncthreads();
-        const long long t = s_tree;
-        if (t >= p.t_end) break;
+        GraphDesc gd;
+        long long t;
+        if (!item_graph(p, s_tree, gd, t)) break;
+        const int n = gd.n, u = gd.u;
         const uint32_t tree = (uint32_t)t;
+        const int nhalf = (n + 1) >> 1;                                // words of one 16-bit array
+        uint16_t *nx16 = reinterpret_cast<uint16_t *>(s_dyn + nhalf);  // successors
+        const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
         if (tid == 0) tmark = clock64();
 
         // ---- 1. cycle popping --------------------------------------------
@@ -713,15 +746,15 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 const bool ok = v < n && v != u;
-                rb[k] = ok ? __ldg(p.rp + v) : 0;
-                deg[k] = ok ? __ldg(p.rp + v + 1) - rb[k] : 0;
+                rb[k] = ok ? __ldg(gd.rp + v) : 0;
+                deg[k] = ok ? __ldg(gd.rp + v + 1) - rb[k] : 0;
             }
             int y[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                const unsigned long long x = philox_x64((uint32_t)v, 0u, tree, p.graph, p.key0, p.key1);
-                y[k] = (deg[k] > 0) ? __ldg(p.ci + rb[k] + (int)__umul64hi(x, (unsigned long long)deg[k])) : -1;
+                const unsigned long long x = philox_x64((uint32_t)v, 0u, tree, gd.graph, p.key0, p.key1);
+                y[k] = (deg[k] > 0) ? __ldg(gd.ci + rb[k] + (int)__umul64hi(x, (unsigned long long)deg[k])) : -1;
             }
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
@@ -827,7 +860,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             for (int i = tid; i < nX; i += BT) {
                 const int x = X[i];
                 const int k = pop[x] + 1;
-                const int y = stack_entry(p, x, (uint32_t)k, tree);
+                const int y = stack_entry(gd, p.key0, p.key1, x, (uint32_t)k, tree);
                 pop[x] = k;
                 nxt[x] = y;
                 nx16[x] = (uint16_t)y;
@@ -894,7 +927,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         }
 
         if (p.mode == 1) {
-            const long long o = (t - p.t_begin) * (long long)n;
+            const long long o = s_tree * (long long)n;
             for (int v = tid; v < n; v += BT) {
                 p.next_out[o + v] = nxt[v];
                 if (p.pops_out) p.pops_out[o + v] = pop[v];
@@ -1065,14 +1098,14 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             if (v == u) continue;
             const uint32_t cv = C[v];
             const int pv = (int)(cv & 0xFFFFu);
-            const int s0 = __ldg(p.pathptr + v);
-            const int d = __ldg(p.pathptr + v + 1) - s0;
+            const int s0 = __ldg(gd.pathptr + v);
+            const int d = __ldg(gd.pathptr + v + 1) - s0;
             int prevb = v, prevnb = (int)(cv >> 16), prevpre = pv;
             int cnt = 0;
             for (int c = 0; c < d; c += kPathChunk) {
                 int a[kPathChunk], na[kPathChunk], pa[kPathChunk], tx[kPathChunk], sg[kPathChunk], lo[kPathChunk];
 #pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(p.path + s0 + c + j) : -1;
+                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
 #pragma unroll
                 for (int j = 0; j < kPathChunk; ++j) {
                     const uint32_t w = (a[j] >= 0) ? C[a[j]] : 0xFFFE0000u;
@@ -1109,7 +1142,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 prevnb = na[kPathChunk - 1];
                 prevpre = pa[kPathChunk - 1];
             }
-            Rp[v] += cnt;
+            if (p.R_direct) {
+                if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
+            } else {
+                Rp[v] += cnt;
+            }
         }
         __syncthreads();
         UST_PHASE(9);
@@ -1142,13 +1179,13 @@ __global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict_
 
 // Shared counters for graphs of at most this many vertices (4 B each, below
 // 2^16 so that two 16-bit halves fit one word).
-constexpr int kSmemMaxN = 56 * 1024;
+constexpr int kSmemMaxN = kSmemMaxVertices;
 
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
-    if (p.n <= kSmemMaxN) {
-        const size_t bytes = (size_t)((p.n + 1) / 2) * 2 * sizeof(uint32_t);
+    if (p.max_n <= kSmemMaxN) {
+        const size_t bytes = (size_t)((p.max_n + 1) / 2) * 2 * sizeof(uint32_t);
         cudaError_t e = cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
@@ -1167,9 +1204,10 @@ int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm)
     if (ctas_per_sm < 1) ctas_per_sm = (block_threads == 1024) ? 1 : 1024 / block_threads;
     c->block_threads = block_threads;
     c->ctas = c->num_sms * ctas_per_sm;
-    c->ws_stride = ((int64_t)c->n + 2 + 31) / 32 * 32;
+    const int64_t nw = c->ws_n > 0 ? c->ws_n : c->n;  // a batch sizes it for its largest graph
+    c->ws_stride = (nw + 2 + 31) / 32 * 32;
     const size_t ws_bytes = (size_t)c->ctas * kWsArrays * (size_t)c->ws_stride * sizeof(int32_t);
-    const size_t rp_bytes = (size_t)c->ctas * (size_t)c->n * sizeof(int32_t);
+    const size_t rp_bytes = (size_t)c->ctas * (size_t)nw * sizeof(int32_t);
     if (cudaMalloc(&c->d_ws, ws_bytes) != cudaSuccess) return fail(c, UST_ENOMEM, "sampler workspace");
     if (cudaMalloc(&c->d_Rp, rp_bytes) != cudaSuccess) return fail(c, UST_ENOMEM, "partial counts");
     return UST_OK;
@@ -1186,22 +1224,41 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
     UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
 
-    SampleParams p;
-    p.n = c->n;
-    p.u = c->pivot;
-    p.graph = (uint32_t)c->graph_id;
+    // the graph's descriptor: uploaded when B_u (pivot, path space) changed
+    GraphDesc gd{};
+    gd.n = c->n;
+    gd.u = c->pivot;
+    gd.graph = (uint32_t)c->graph_id;
+    gd.voff = 0;
+    gd.tree_begin = 0;
+    gd.rp = c->d_rp;
+    gd.ci = c->d_ci;
+    gd.bpar = c->d_bpar;
+    gd.path = c->d_path;
+    gd.pathptr = c->d_pathptr;
+    const GraphDesc &o = c->single_desc;
+    const bool same = o.n == gd.n && o.u == gd.u && o.graph == gd.graph && o.rp == gd.rp && o.ci == gd.ci &&
+                      o.bpar == gd.bpar && o.path == gd.path && o.pathptr == gd.pathptr;
+    if (!c->single_desc_valid || !same) {
+        c->single_desc = gd;
+        const long long starts[2] = {0, kOpenEnd};
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_graphs, &c->single_desc, sizeof(GraphDesc), cudaMemcpyHostToDevice,
+                                     c->stream));
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_items, starts, sizeof(starts), cudaMemcpyHostToDevice, c->stream));
+        c->single_desc_valid = true;
+    }
+    SampleParams p{};
+    p.max_n = c->n;
     p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
     p.key1 = (uint32_t)(seed >> 32);
-    p.rp = c->d_rp;
-    p.ci = c->d_ci;
-    p.bpar = c->d_bpar;
-    p.path = c->d_path;
-    p.pathptr = c->d_pathptr;
+    p.graphs = c->d_graphs;
+    p.ngraphs = 1;
+    p.item_start = c->d_items;
+    p.total_items = t1 - t0;
+    p.tree_offset = t0;
     p.ws = c->d_ws;
     p.stride = c->ws_stride;
     p.Rp = c->d_Rp;
-    p.t_begin = t0;
-    p.t_end = t1;
     unsigned long long *st = reinterpret_cast<unsigned long long *>(c->d_stats);
     p.next_tree = st + 4;
     p.stats = st;
@@ -1283,6 +1340,7 @@ constexpr int kNoAllocThreads = 256;
 constexpr long long kNoAllocStride = ((kNoAllocMaxN + 2 + 31) / 32) * 32;
 // layout in int32 words: sampler workspace | partial counts | dist | bfs parent
 //                        | path offsets | paths | stats (32 x int64)
+//                        | graph descriptor and item starts
 constexpr long long kNaWs = 0;
 constexpr long long kNaRp = kNaWs + (long long)kNoAllocCtas * kWsArrays * kNoAllocStride;
 constexpr long long kNaDist = kNaRp + (long long)kNoAllocCtas * kNoAllocMaxN;
@@ -1290,7 +1348,10 @@ constexpr long long kNaBpar = kNaDist + kNoAllocMaxN;
 constexpr long long kNaPathPtr = kNaBpar + kNoAllocMaxN;
 constexpr long long kNaPath = kNaPathPtr + ((kNoAllocMaxN + 1 + 31) / 32) * 32;
 constexpr long long kNaStats = kNaPath + kNoAllocMaxPath;
-constexpr long long kNaWords = kNaStats + 2 * 32;
+constexpr long long kNaDesc = kNaStats + 2 * 32;  // one GraphDesc and two item starts
+constexpr long long kNaWords = kNaDesc + 64;
+static_assert(sizeof(GraphDesc) + 2 * sizeof(long long) <= 64 * sizeof(int32_t), "descriptor slot");
+static_assert((kNaDesc * sizeof(int32_t)) % 16 == 0, "descriptor alignment");
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNaWords];
 
@@ -1299,10 +1360,9 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[kNaWords];
 // the flattened paths. Errors go to status (bit 1: disconnected, bit 2: too
 // many path entries).
 constexpr int kPrepThreads = 1024;
-__global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, int u, const int32_t *__restrict__ rp,
-                                                                       const int32_t *__restrict__ ci, int32_t *dist,
-                                                                       int32_t *bpar, int32_t *pathptr, int32_t *path,
-                                                                       int path_cap, int *status)
+__device__ void prepare_graph(int n, int u, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              int32_t *dist, int32_t *bpar, int32_t *pathptr, int32_t *path, long long path_cap,
+                              int *status, int *ecc_out = nullptr, int *fc_out = nullptr)
 {
     __shared__ int s_warp[kPrepThreads / 32 + 1];
     __shared__ int s_bad;
@@ -1313,7 +1373,8 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    for (int level = 0; level < n; ++level) {
+    int level = 0;
+    for (; level < n; ++level) {
         int any = 0;
         for (int v = tid; v < n; v += kPrepThreads) {
             if (dist[v] >= 0) continue;
@@ -1329,6 +1390,7 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
         }
         if (!__syncthreads_or(any)) break;
     }
+    if (ecc_out && tid == 0) *ecc_out = level;
     // exclusive prefix of dist (unreached vertices flag the graph as disconnected)
     int carry = 0;
     for (int base = 0; base < n; base += kPrepThreads) {
@@ -1360,7 +1422,10 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
         carry += s_warp[32];
         __syncthreads();
     }
-    if (tid == 0) pathptr[n] = carry;
+    if (tid == 0) {
+        pathptr[n] = carry;
+        if (fc_out) *fc_out = carry;
+    }
     if (s_bad || carry > path_cap) {
         if (tid == 0) *status |= s_bad ? 1 : 2;
         return;
@@ -1375,6 +1440,32 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
             path[k++] = x;
         }
     }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, int u, uint32_t graph,
+                                                                       const int32_t *__restrict__ rp,
+                                                                       const int32_t *__restrict__ ci, int32_t *dist,
+                                                                       int32_t *bpar, int32_t *pathptr, int32_t *path,
+                                                                       int path_cap, int *status, GraphDesc *desc,
+                                                                       long long *item_start)
+{
+    if (threadIdx.x == 0) {
+        GraphDesc d;
+        d.n = n;
+        d.u = u;
+        d.graph = graph;
+        d.voff = 0;
+        d.tree_begin = 0;
+        d.rp = rp;
+        d.ci = ci;
+        d.bpar = bpar;
+        d.path = path;
+        d.pathptr = pathptr;
+        *desc = d;
+        item_start[0] = 0;
+        item_start[1] = kOpenEnd;
+    }
+    prepare_graph(n, u, rp, ci, dist, bpar, pathptr, path, path_cap, status);
 }
 
 // Device address of g_noalloc_scratch, looked up once per device.
@@ -1416,8 +1507,10 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
     if (cudaMemsetAsync(Rp, 0, (size_t)kNoAllocCtas * n * sizeof(int32_t), st) != cudaSuccess) return UST_ECUDA;
     if (cudaMemsetAsync(R_out, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess) return UST_ECUDA;
     int *status = reinterpret_cast<int *>(stats + 5);
-    noalloc_prepare_kernel<<<1, kPrepThreads, 0, st>>>(n, pivot, row_ptr, col_idx, dist, bpar, pathptr, path,
-                                                        kNoAllocMaxPath, status);
+    GraphDesc *desc = reinterpret_cast<GraphDesc *>(base + kNaDesc);
+    long long *item_start = reinterpret_cast<long long *>(desc + 1);
+    noalloc_prepare_kernel<<<1, kPrepThreads, 0, st>>>(n, pivot, (uint32_t)graph_id, row_ptr, col_idx, dist, bpar,
+                                                        pathptr, path, kNoAllocMaxPath, status, desc, item_start);
     if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
     unsigned long long h_stats[32];
     if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess) return UST_ECUDA;
@@ -1427,22 +1520,18 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
     int ecc = 0;
     if (t1 > t0) {
         ecc = n;  // upper bound on ecc(u), used only for the popping-round limit
-        SampleParams p;
-        p.n = n;
-        p.u = pivot;
-        p.graph = (uint32_t)graph_id;
+        SampleParams p{};
+        p.max_n = n;
         p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
         p.key1 = (uint32_t)(seed >> 32);
-        p.rp = row_ptr;
-        p.ci = col_idx;
-        p.bpar = bpar;
-        p.path = path;
-        p.pathptr = pathptr;
+        p.graphs = desc;
+        p.ngraphs = 1;
+        p.item_start = item_start;
+        p.total_items = t1 - t0;
+        p.tree_offset = t0;
         p.ws = ws;
         p.stride = kNoAllocStride;
         p.Rp = Rp;
-        p.t_begin = t0;
-        p.t_end = t1;
         p.next_tree = stats + 4;
         p.stats = stats;
         p.status = status;
@@ -1465,3 +1554,115 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
     }
     return UST_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batches of graphs: B_u of every graph in one launch (one CTA per graph) and
+// the sampler over (graph, tree) work items.
+namespace ust {
+namespace {
+
+// out: status of graph g at [g], ecc(u) at [count + g], f^c(u) at [2 count + g]
+__global__ void __launch_bounds__(kPrepThreads) batch_prepare_kernel(const PrepDesc *__restrict__ d, int count,
+                                                                     int *out)
+{
+    const PrepDesc g = d[blockIdx.x];
+    prepare_graph(g.n, g.u, g.rp, g.ci, g.dist, g.bpar, g.pathptr, g.path, g.path_cap, out + blockIdx.x,
+                  out + count + blockIdx.x, out + 2 * count + blockIdx.x);
+}
+
+// diag of graph blockIdx.x: L^+[u,u] = x_u, L^+[v,v] = (R[v]/tau - x_u) + 2 x_v
+__global__ void batch_combine_kernel(const CombineDesc *__restrict__ d, const long long *__restrict__ R,
+                                     const double *__restrict__ x, double *__restrict__ diag)
+{
+    const CombineDesc g = d[blockIdx.x];
+    const double xu = x[g.voff + g.u];
+    const double tau = (double)g.trees;
+    for (int v = threadIdx.x; v < g.n; v += blockDim.x) {
+        const long long i = g.voff + v;
+        if (v == g.u) {
+            diag[i] = xu;
+        } else {
+            const double r = __ddiv_rn((double)R[i], tau);
+            const double t = __dsub_rn(r, xu);
+            diag[i] = __dadd_rn(t, __dmul_rn(2.0, x[i]));
+        }
+    }
+}
+
+}  // namespace
+
+int run_batch_prepare(Ctx *c, const PrepDesc *d_desc, int count, int *d_out)
+{
+    batch_prepare_kernel<<<count, kPrepThreads, 0, c->stream>>>(d_desc, count, d_out);
+    c->launches += 1;
+    UST_CUDA_TRY(cudaGetLastError());
+    return UST_OK;
+}
+
+int run_batch_combine(Ctx *c, const CombineDesc *d_desc, int count, double *d_diag)
+{
+    phase_begin(c, Ctx::kEvCombine);
+    batch_combine_kernel<<<count, 256, 0, c->stream>>>(d_desc, reinterpret_cast<const long long *>(c->d_R), c->d_x,
+                                                       d_diag);
+    phase_end(c, Ctx::kEvCombine);
+    c->launches += 1;
+    UST_CUDA_TRY(cudaGetLastError());
+    return UST_OK;
+}
+
+int run_batch_sampler(Ctx *c, const GraphDesc *d_graphs, const long long *d_item_start, int ngraphs,
+                      long long total_items, int max_n, long long max_rounds, uint64_t seed, int64_t *d_R,
+                      int64_t *draws, int64_t *rounds, int *max_round_count, int *max_pops)
+{
+    if (total_items <= 0) return UST_OK;
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
+    SampleParams p{};
+    p.max_n = max_n;
+    p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+    p.key1 = (uint32_t)(seed >> 32);
+    p.ws = c->d_ws;
+    p.stride = c->ws_stride;
+    p.Rp = c->d_Rp;
+    p.tree_offset = 0;
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(c->d_stats);
+    p.next_tree = st + 4;
+    p.stats = st;
+    p.status = reinterpret_cast<int *>(st + 5);
+    p.max_rounds = (int)std::min<long long>(max_rounds, 1ll << 30);
+    int lg = 0;
+    while ((1ll << lg) < (long long)max_n) ++lg;
+    p.max_steps = lg + 4;
+    p.mode = 0;
+    p.graphs = d_graphs;
+    p.ngraphs = ngraphs;
+    p.item_start = d_item_start;
+    p.total_items = total_items;
+    p.R_direct = reinterpret_cast<unsigned long long *>(d_R);
+    const int grid = (int)std::min<long long>(c->ctas, total_items);
+    cudaError_t e;
+    phase_begin(c, Ctx::kEvSample);
+    switch (c->block_threads) {
+    case 256: e = launch_sampler<256>(grid, c->stream, p); break;
+    case 1024: e = launch_sampler<1024>(grid, c->stream, p); break;
+    default: e = launch_sampler<512>(grid, c->stream, p); break;
+    }
+    phase_end(c, Ctx::kEvSample);
+    c->launches += 1;
+    if (e != cudaSuccess) return fail(c, UST_ECUDA, std::string("batch sampler launch: ") + cudaGetErrorString(e));
+    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 32 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const int status = (int)c->h_stats[5];
+    if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
+    if (status & kStatusJumpSteps) return fail(c, UST_ETIMEOUT, "pointer jumping did not converge");
+    if (status) return fail(c, UST_ECUDA, "sampler reported an inconsistent state");
+    c->last_trees = total_items;
+    c->last_draws = c->h_stats[0];
+    for (int k = 0; k < 12; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
+    if (draws) *draws = c->h_stats[0];
+    if (rounds) *rounds = c->h_stats[1];
+    if (max_round_count) *max_round_count = (int)c->h_stats[2];
+    if (max_pops) *max_pops = (int)c->h_stats[3];
+    return UST_OK;
+}
+
+}  // namespace ust

@@ -1,0 +1,95 @@
+"""Batches of graphs (ust_init_batch): every graph's counts, column and
+diagonal equal those of a single-graph context for the same graph, pivot and
+graph id, and the counts equal the oracle's."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2006_13679_gb300 as p
+    p.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.lib()
+    return oracle
+
+
+def small_batch():
+    gs = [synth.grid(20, 15), synth.ba(3000, 4, seed=1), synth.er(2500, 8.0, seed=2), synth.path(40),
+          synth.rmat(11, 8, seed=3), synth.ba(60000, 3, seed=4)]  # the last exceeds the shared-memory sampler
+    return gs, [synth.max_degree_vertex(g) for g in gs]
+
+
+def test_batch_equals_single_graph_contexts(pkg, orc):
+    gs, piv = small_batch()
+    base = 11
+    with pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], piv, graph_id=base) as b:
+        assert b.count == len(gs) and b.n == sum(g.n for g in gs)
+        b.sample_aggregate(40, 9)
+        b.sample_aggregate(60, 9)  # tree ids continue per graph
+        R = b.split(b.counts())
+        x = b.split(b.column())
+        d = b.split(b.diag())
+        for i, g in enumerate(gs):
+            info = b.graph_info(i)
+            assert info["n"] == g.n and info["trees"] == 100 and info["pivot"] == piv[i]
+            with pkg.UST(g.row_ptr, g.col_idx, piv[i], graph_id=base + i) as h:
+                h.sample_aggregate(100, 9)
+                assert np.array_equal(R[i], h.counts()), i
+                np.testing.assert_allclose(x[i], h.column(), rtol=0, atol=1e-12)
+                np.testing.assert_allclose(d[i], h.diag(), rtol=1e-12, atol=1e-12)
+            ecc, _, par = orc.bfs(g, piv[i])
+            assert info["ecc"] == ecc
+            R_ref, _ = orc.sample_aggregate(g, piv[i], par, 0, 100, 9, graph=base + i, threads=THREADS)
+            assert np.array_equal(R[i], R_ref), i
+            np.testing.assert_allclose(d[i], orc.combine(R[i], 100, x[i], piv[i]), rtol=1e-12, atol=0)
+
+
+def test_batch_tops_up_each_graph_to_its_tau(pkg, orc):
+    gs = [synth.grid(6, 6), synth.cycle(30), synth.complete(12)]
+    piv = [14, 0, 3]
+    with pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], piv) as b:
+        b.diag(1.5)
+        for i, g in enumerate(gs):
+            ecc, _, _ = orc.bfs(g, piv[i])
+            assert b.graph_info(i)["trees"] == orc.tau(ecc, g.m, 1.5, 1.0 / g.n, 0.3)
+
+
+def test_batch_rejects_disconnected_graph(pkg):
+    gs = [synth.grid(5, 5), synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], lcc=False)]
+    with pytest.raises(pkg.UstError) as e:
+        pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], [0, 0])
+    assert e.value.code == pkg.UST_ENOTCONNECTED
+
+
+def test_batch_of_256_uneven_graphs(pkg, orc):
+    """The batch workload: 256 BA/ER largest components with n in [1k, 64k]
+    and average degree in [8, 32], max-degree pivots, 1024 trees each; counts
+    of sampled graphs against the oracle."""
+    specs = synth.batch_specs(256)
+    gs = [synth.batch_graph(s) for s in specs]
+    piv = [synth.max_degree_vertex(g) for g in gs]
+    with pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], piv, skip_validation=True) as b:
+        b.sample_aggregate(1024, 0)
+        R = b.split(b.counts())
+        d = b.split(b.diag())
+        x = b.split(b.column())
+        for i in [0, 1, 127, 255, int(np.argmax([g.n for g in gs]))]:
+            g = gs[i]
+            _, _, par = orc.bfs(g, piv[i])
+            R_ref, _ = orc.sample_aggregate(g, piv[i], par, 0, 1024, 0, graph=i, threads=THREADS)
+            assert np.array_equal(R[i], R_ref), i
+            np.testing.assert_allclose(d[i], orc.combine(R[i], 1024, x[i], piv[i]), rtol=1e-12, atol=0)
