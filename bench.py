@@ -35,7 +35,7 @@ SEED = 0
 # DRAM bytes (read + write) of one sampler launch on the rmat16 workload, from the ncu capture
 # summarised in profiles/sample_aggregate_rmat16.md. Reported only while the kernel source is
 # the one the capture was taken on.
-TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "2a17e8705ca68e52fcd689477bbdce1dffe37d0c", "bytes": 1.841372e9 + 4.048805e9}
+TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "f477f1df45caf052fcb03224094f8af600da153d", "bytes": 1.680338e9 + 3.968391e9}
 
 # workload -> (description, oracle sample in trees for the CPU baseline; None = all)
 WORKLOADS = {
@@ -44,7 +44,14 @@ WORKLOADS = {
     "hyperbolic20": ("random hyperbolic graph n=2^20, avg degree 20, exponent 3, T=0, LCC, max-degree pivot, "
                      "tau(eps=0.3)", 256),
     "rmat22": ("R-MAT scale 22, edge factor 16, LCC, max-degree pivot, tau(eps=0.3)", 96),
+    "batch256": ("256 graphs: even index Barabasi-Albert (k = avg/2), odd index Erdos-Renyi, n ~ U[1000, 64000], "
+                 "average degree ~ U[8, 32], LCC, per-graph max-degree pivot, 1024 trees each", None),
 }
+BATCH_GRAPHS = 256
+BATCH_TREES = 1024
+# CPU baseline sample of the batch workload: the first graphs, this many trees each
+BATCH_CPU_GRAPHS = 16
+BATCH_CPU_TREES = 64
 
 # Algorithmic bytes (what the method must touch, no cache effects):
 #   per Wilson draw: row_ptr pair 8 B + col_idx 4 B + successor write 4 B + stack depth 4 B
@@ -154,6 +161,9 @@ def run_reference(args, rank: int, world: int) -> None:
         return
     import oracle
     import synth
+    if args.workload == "batch256":
+        run_reference_batch(args, world)
+        return
     g, u, T0, eps = synth.workload(args.workload)
     T = workload_trees(g, u, T0, eps)
     threads = oracle.max_threads()
@@ -184,6 +194,198 @@ def run_reference(args, rank: int, world: int) -> None:
                              "sample": f"{sample} trees of the workload per step"},
             "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_workload():
+    import synth
+    gs = [synth.batch_graph(sp) for sp in synth.batch_specs(BATCH_GRAPHS)]
+    return gs, [synth.max_degree_vertex(g) for g in gs]
+
+
+def oracle_batch_sample(gs, pivots, threads):
+    """The oracle on the CPU sample of the batch: BFS, trees, FP64 CG and the
+    combination for the first BATCH_CPU_GRAPHS graphs, BATCH_CPU_TREES trees
+    each (graph id = index). Returns (trees, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    for i in range(BATCH_CPU_GRAPHS):
+        g, u = gs[i], pivots[i]
+        _, _, par = oracle.bfs(g, u)
+        R, _ = oracle.sample_aggregate(g, u, par, 0, BATCH_CPU_TREES, SEED, graph=i, threads=threads)
+        x, _, _, _ = oracle.cg(g, u, tol=1e-9)
+        oracle.combine(R, BATCH_CPU_TREES, x, u)
+    return BATCH_CPU_GRAPHS * BATCH_CPU_TREES, time.perf_counter() - t0
+
+
+def run_reference_batch(args, world: int) -> None:
+    import oracle
+    gs, pivots = batch_workload()
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle_batch_sample(gs, pivots, threads)
+    times = []
+    trees = 0
+    for _ in range(args.steps):
+        trees, sec = oracle_batch_sample(gs, pivots, threads)
+        times.append(sec)
+    sec = statistics.mean(times)
+    value = trees / sec
+    sample = (f"BFS + {BATCH_CPU_TREES} trees + FP64 CG + combine for each of the first {BATCH_CPU_GRAPHS} "
+              f"of the {BATCH_GRAPHS} graphs per step")
+    line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"batch256: {WORKLOADS['batch256'][0]}; total n={sum(g.n for g in gs)}",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "trees/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch_gpu(args, rank: int, world: int, local_rank: int, dist) -> None:
+    """The batch workload: one step = B_u of every graph, 1024 trees of every
+    graph through the batched sampler launches, every graph's column solve
+    and the diagonals. The comparator loops the single-graph path over the
+    same graphs (same tree ids and graph words, so the counts must match)."""
+    import numpy as np
+    import torch
+
+    import paper_2006_13679_gb300 as pkg
+
+    gs, pivots = batch_workload()
+    T = BATCH_TREES
+    seed = SEED + rank
+    ntot = sum(g.n for g in gs)
+    stream = torch.cuda.Stream()
+    b = pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], pivots, stream=stream, skip_validation=True)
+    diag_d = torch.empty(ntot, dtype=torch.float64, device="cuda")
+    counts_d = torch.empty(ntot, dtype=torch.int64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        b.reset()                     # B_u of every graph, clear R and columns
+        b.sample_aggregate(T, seed)   # T trees of every graph
+        if dist is not None:
+            b.counts(counts_d)
+            with torch.cuda.stream(stream):
+                dist.all_reduce(counts_d)
+        b.diag(0.0, diag_d)           # every graph's column solve + combination
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sample_ms, bfs_ms, solve_ms, draws = [], [], [], []
+    launches0 = b.info()["kernel_launches"]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index(local_rank)) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0[k].record(stream)
+            step()
+            ev1[k].record(stream)
+            inf = b.info()
+            sample_ms.append(inf["sample_ms"])
+            bfs_ms.append(inf["bfs_ms"])
+            solve_ms.append(inf["solve_ms"])
+            draws.append(inf["last_draws"])
+        torch.cuda.synchronize()
+    launches = b.info()["kernel_launches"] - launches0
+    if dist is not None:
+        dist.barrier()
+    ms = statistics.mean(a.elapsed_time(c) for a, c in zip(ev0, ev1))
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    trees_step = len(gs) * T
+    value = world * trees_step / (ms / 1e3)
+    clocks = clk.summary()
+    info = b.info()
+    kernel_ms = statistics.mean(sample_ms)
+    farness = [b.graph_info(i)["farness"] for i in range(len(gs))]
+    alg = BYTES_PER_DRAW * int(statistics.mean(draws)) + sum(
+        T * (BYTES_PER_VERTEX * g.n + BYTES_PER_PAIR * f) for g, f in zip(gs, farness))
+    peak, peak_kind = peaks()
+    achieved = alg / (kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sample_aggregate_smem_kernel + sample_aggregate_kernel (batch launches)",
+                "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_kind": peak_kind}
+    R_batch = b.counts()
+
+    # comparator: the single-graph path looped over the graphs (contexts
+    # created outside the timed regions; each graph timed on the same stream)
+    comparator = None
+    if not args.no_comparator:
+        loop_ms = 0.0
+        same = True
+        off = b.offsets()
+        for i, (g, u) in enumerate(zip(gs, pivots)):
+            with pkg.UST(g.row_ptr, g.col_idx, u, stream=stream, skip_validation=True, graph_id=i) as h:
+                out = diag_d[off[i]:off[i + 1]]
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.reset(u)
+                h.sample_aggregate(T, seed)
+                h.diag(0.0, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                loop_ms += e0.elapsed_time(e1)
+                same = same and bool(np.array_equal(h.counts(), R_batch[off[i]:off[i + 1]]))
+        comparator = {"form": "single-graph path looped over the 256 graphs (one context per graph)",
+                      "ms_per_step": loop_ms, "value": trees_step / (loop_ms / 1e3), "unit": "trees/s",
+                      "batched_speedup": loop_ms / ms, "counts_equal_to_batch": same}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h2d = sum((g.n + 1) * 4 + g.nnz * 4 for g in gs)
+        d2h = ntot * 8
+        secs = []
+        for k in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], pivots) as be:
+                be.sample_aggregate(T, seed)
+                be.diag()
+            if k > 0:
+                secs.append(time.perf_counter() - t0)
+        e2e = {"value": trees_step / statistics.mean(secs), "unit": "trees/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(secs) * 1e3}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            threads = oracle.max_threads()
+            trees_cpu, sec = oracle_batch_sample(gs, pivots, threads)
+            cpu = {"value": trees_cpu / sec, "unit": "trees/s", "cores": threads, "kind": "oracle",
+                   "sample": f"BFS + {BATCH_CPU_TREES} trees + FP64 CG + combine for each of the first "
+                             f"{BATCH_CPU_GRAPHS} of the {len(gs)} graphs, OpenMP over trees", "seconds": sec}
+        line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": f"batch256: {WORKLOADS['batch256'][0]}; total n={ntot}, "
+                                       f"total arcs={sum(g.nnz for g in gs)}, {T} trees per graph per GPU, "
+                                       f"seed {SEED}+rank",
+                           "l2": "flushed between timed steps (256 MB write); inputs exceed L2",
+                           "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads"},
+                "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,
+                                            "solve": statistics.mean(solve_ms)},
+                "draws_per_tree": statistics.mean(draws) / trees_step, "cg_iters": info["cg_iters"],
+                "cg_relres": info["cg_relres"], "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+                "gpu_launches_per_step": launches / args.steps, "e2e": e2e, "cpu_baseline": cpu,
+                "comparator": comparator}
+        print(json.dumps(line), flush=True)
+    b.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def cpu_baseline(g, u, T, sample) -> dict:
@@ -236,6 +438,9 @@ def main() -> None:
         dist.init_process_group("nccl")
 
     pkg.build()
+    if args.workload == "batch256":
+        run_batch_gpu(args, rank, world, local_rank, dist)
+        return
     g, u, T0, eps = synth.workload(args.workload)
     T = workload_trees(g, u, T0, eps)
     seed = SEED + rank

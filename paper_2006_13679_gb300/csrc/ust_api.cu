@@ -49,6 +49,12 @@ void release(Ctx *c)
     cudaFree(c->d_items);
     cudaFree(c->d_comb);
     cudaFree(c->d_prep);
+    cudaFree(c->d_tasks);
+    cudaFree(c->d_results);
+    cudaFreeHost(c->h_results);
+    cudaFree(c->d_bw32);
+    cudaFree(c->d_bw64);
+    cudaFree(c->d_br64);
     cudaFree(c->d_prep_out);
     cudaFreeHost(c->h_prep_out);
     for (int i = 0; i < 2 * Ctx::kEvPhases; ++i)
@@ -262,8 +268,8 @@ int ust_batch_graph_info(const ust_ctx *h, int32_t g, ust_info *out)
     out->trees = c->btrees[g];
     out->seed = c->seed;
     out->farness = c->bfarness[g];
-    out->sample_ctas = c->ctas;
-    out->sample_threads = c->block_threads;
+    out->sample_ctas = c->class_cfg[c->bclass[g]].ctas;
+    out->sample_threads = c->class_cfg[c->bclass[g]].bt;
     return UST_OK;
 }
 
@@ -428,8 +434,12 @@ int ust_get_info(const ust_ctx *h, ust_info *out)
     out->cg_iters = c->cg_iters;
     out->cg_refinements = c->cg_refinements;
     out->cg_relres = c->cg_relres;
-    out->sample_ctas = c->ctas;
-    out->sample_threads = c->block_threads;
+    ust::LaunchCfg shape = c->cfg;  // a batch reports the shape of its largest graphs
+    if (c->batch)
+        for (int k = 0; k < ust::kNumClasses; ++k)
+            if (c->class_maxn[k] > 0) shape = c->class_cfg[k];
+    out->sample_ctas = shape.ctas;
+    out->sample_threads = shape.bt;
     out->kernel_launches = c->launches;
     out->last_trees = c->last_trees;
     out->last_draws = c->last_draws;

@@ -92,21 +92,23 @@ int batch_sample(Ctx *c, const std::vector<int64_t> &count, uint64_t seed)
     const int B = c->batch;
     std::vector<GraphDesc> descs;
     std::vector<long long> starts;
-    long long total[2] = {0, 0};
-    int ngr[2] = {0, 0}, maxn[2] = {0, 0};
+    long long total[kNumClasses] = {};
+    int ngr[kNumClasses] = {}, maxn[kNumClasses] = {};
     long long max_rounds = 1024;
-    std::vector<int> group[2];
+    std::vector<int> group[kNumClasses];
     for (int g = 0; g < B; ++g) {
         if (count[g] <= 0) continue;
         if (c->btrees[g] + count[g] > (int64_t)0xFFFFFFFFll) return fail(c, UST_EINVAL, "tree ids must stay below 2^32");
-        const int k = (c->bn[g] <= kSmemMaxVertices) ? 0 : 1;
-        group[k].push_back(g);
+        group[c->bclass[g]].push_back(g);
         max_rounds = std::max<long long>(max_rounds,
                                          16ll * ((long long)c->bnnz[g] * std::max(1, c->becc[g]) + c->bn[g]) + 1024);
     }
     if (c->max_pop_rounds > 0) max_rounds = c->max_pop_rounds;
-    // descriptors: group 0 at [0, |group 0|), group 1 after it; item starts likewise
-    for (int k = 0; k < 2; ++k) {
+    // descriptors class after class; item starts likewise (|class| + 1 each)
+    int desc_at[kNumClasses] = {}, start_at[kNumClasses] = {};
+    for (int k = 0; k < kNumClasses; ++k) {
+        desc_at[k] = (int)descs.size();
+        start_at[k] = (int)starts.size();
         long long acc = 0;
         for (int g : group[k]) {
             descs.push_back(desc_of(c, g, c->btrees[g]));
@@ -125,20 +127,25 @@ int batch_sample(Ctx *c, const std::vector<int64_t> &count, uint64_t seed)
                                  c->stream));
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_Rtmp, c->d_R, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
     int64_t draws_total = 0, rounds_total = 0;
-    for (int k = 0; k < 2; ++k) {
+    phase_open(c, Ctx::kEvSample);  // both launches in one timed phase
+    for (int k = 0; k < kNumClasses; ++k) {
         if (total[k] == 0) continue;
-        const GraphDesc *dg = c->d_graphs + (k == 0 ? 0 : ngr[0]);
-        const long long *di = c->d_items + (k == 0 ? 0 : ngr[0] + 1);
+        const GraphDesc *dg = c->d_graphs + desc_at[k];
+        const long long *di = c->d_items + start_at[k];
         int64_t draws = 0, rounds = 0;
         int mr = 0, mp = 0;
-        const int rc = run_batch_sampler(c, dg, di, ngr[k], total[k], maxn[k], max_rounds, seed, c->d_Rtmp, &draws,
-                                         &rounds, &mr, &mp);
-        if (rc) return rc;
+        const int rc = run_batch_sampler(c, c->class_cfg[k], dg, di, ngr[k], total[k], maxn[k], max_rounds, seed,
+                                         c->d_Rtmp, &draws, &rounds, &mr, &mp);
+        if (rc) {
+            c->ev_hold[Ctx::kEvSample] = false;
+            return rc;
+        }
         draws_total += draws;
         rounds_total += rounds;
         c->max_rounds_seen = std::max(c->max_rounds_seen, mr);
         c->max_depth_seen = std::max(c->max_depth_seen, mp);
     }
+    phase_close(c, Ctx::kEvSample);
     std::swap(c->d_R, c->d_Rtmp);
     int64_t trees = 0;
     for (int g = 0; g < B; ++g) {
@@ -156,27 +163,29 @@ int batch_sample(Ctx *c, const std::vector<int64_t> &count, uint64_t seed)
 
 int batch_solve(Ctx *c)
 {
-    int iters = 0, refinements = 0;
-    double worst = 0.0;
-    for (int g = 0; g < c->batch; ++g) {
-        SolveView v;
-        v.n = c->bn[g];
-        v.u = c->bpivot[g];
-        v.rp = c->d_rp + c->bvoff[g] + g;
-        v.ci = c->d_ci + c->baoff[g];
-        v.heavy = c->d_heavy + c->bhoff[g];
-        v.n_heavy = c->bheavy_n[g];
-        v.blocks = c->bblocks[g];
-        v.x = c->d_x + c->bvoff[g];
-        const int rc = run_solve_view(c, v);
-        if (rc) return rc;
-        iters += c->cg_iters;
-        refinements = std::max(refinements, c->cg_refinements);
-        worst = std::max(worst, c->cg_relres);
+    // every graph's column in one launch, one CTA per graph
+    const int B = c->batch;
+    if (c->solve_fp64 && !c->d_bw64) {
+        if (cudaMalloc(&c->d_bw64, 5 * (size_t)c->n * sizeof(double)) != cudaSuccess)
+            return fail(c, UST_ENOMEM, "FP64 solver vectors");
     }
-    c->cg_iters = iters;
-    c->cg_refinements = refinements;
-    c->cg_relres = worst;
+    std::vector<SolveTask> tasks((size_t)B);
+    for (int g = 0; g < B; ++g) {
+        SolveTask &t = tasks[g];
+        t.n = c->bn[g];
+        t.u = c->bpivot[g];
+        t.rp = c->d_rp + c->bvoff[g] + g;
+        t.ci = c->d_ci + c->baoff[g];
+        t.heavy = c->d_heavy + c->bhoff[g];
+        t.n_heavy = c->bheavy_n[g];
+        t.x = c->d_x + c->bvoff[g];
+        t.r64 = c->d_br64 + c->bvoff[g];
+        t.w = c->solve_fp64 ? (void *)(c->d_bw64 + 5 * c->bvoff[g]) : (void *)(c->d_bw32 + 5 * c->bvoff[g]);
+    }
+    UST_CUDA_TRY(cudaMemcpyAsync(c->d_tasks, tasks.data(), (size_t)B * sizeof(SolveTask), cudaMemcpyHostToDevice,
+                                 c->stream));
+    const int rc = run_solve_cta(c, c->d_tasks, B, c->d_results, c->h_results, c->solve_fp64);
+    if (rc) return rc;
     c->x_valid = true;
     return UST_OK;
 }
@@ -194,7 +203,6 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
     c->bvoff.assign(B + 1, 0);
     c->baoff.assign(B + 1, 0);
     c->btrees.assign(B, 0);
-    int max_n = 0;
     for (int g = 0; g < B; ++g) {
         if (!gs[g].row_ptr || !gs[g].col_idx || gs[g].n < 2 || gs[g].nnz < 2 || pivots[g] < 0 ||
             pivots[g] >= gs[g].n)
@@ -204,14 +212,20 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
         c->bpivot[g] = pivots[g];
         c->bvoff[g + 1] = c->bvoff[g] + gs[g].n;
         c->baoff[g + 1] = c->baoff[g] + gs[g].nnz;
-        max_n = std::max(max_n, gs[g].n);
     }
     if (c->bvoff[B] > 0x7FFFFFF0ll || c->baoff[B] > 0x7FFFFFF0ll)
         return fail(c, UST_EINVAL, "batch too large for 32-bit indices");
     c->n = (int)c->bvoff[B];
     c->nnz = (int)c->baoff[B];
     c->pivot = pivots[0];
-    c->ws_n = max_n;
+    c->bclass.assign(B, 0);
+    for (int k = 0; k < kNumClasses; ++k) c->class_maxn[k] = 0;
+    for (int g = 0; g < B; ++g) {
+        int k = 0;
+        while (c->bn[g] > kClassMaxN[k]) ++k;
+        c->bclass[g] = k;
+        c->class_maxn[k] = std::max(c->class_maxn[k], c->bn[g]);
+    }
 
     // host copies of the row pointers (validation, heavy rows)
     std::vector<int32_t> hrp((size_t)c->n + B);
@@ -251,7 +265,8 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
     if (cudaMalloc(&c->d_R, nv * 8) != cudaSuccess) return fail(c, UST_ENOMEM, "counts");
     if (cudaMalloc(&c->d_Rtmp, nv * 8) != cudaSuccess) return fail(c, UST_ENOMEM, "counts");
     if (cudaMalloc(&c->d_graphs, (size_t)B * sizeof(GraphDesc)) != cudaSuccess) return fail(c, UST_ENOMEM, "graphs");
-    if (cudaMalloc(&c->d_items, ((size_t)B + 2) * sizeof(long long)) != cudaSuccess) return fail(c, UST_ENOMEM, "items");
+    if (cudaMalloc(&c->d_items, ((size_t)B + kNumClasses) * sizeof(long long)) != cudaSuccess)
+        return fail(c, UST_ENOMEM, "items");
     if (cudaMalloc(&c->d_comb, (size_t)B * sizeof(CombineDesc)) != cudaSuccess) return fail(c, UST_ENOMEM, "combine");
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_rp, hrp.data(), hrp.size() * 4, cudaMemcpyHostToDevice, c->stream));
     for (int g = 0; g < B; ++g) {
@@ -284,40 +299,33 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
     c->ecc = *std::max_element(c->becc.begin(), c->becc.end());
     c->farness = c->bpoff[B];
 
-    rc = alloc_sampler(c, op.block_threads, op.ctas_per_sm);
+    rc = alloc_batch_sampler(c, op.block_threads, op.ctas_per_sm);
     if (rc) return rc;
 
-    // solver: scratch for the largest graph, one column slot per vertex,
-    // heavy rows per graph
+    // solver: heavy rows per graph, the columns, and the one-CTA solve's
+    // scratch for every graph at once
     c->bheavy_n.assign(B, 0);
-    c->bblocks.assign(B, 1);
     c->bhoff.assign(B + 1, 0);
     std::vector<int32_t> heavy;
-    int max_parts = 1;
     for (int g = 0; g < B; ++g) {
         const int32_t *r = hrp.data() + c->bvoff[g] + g;
         for (int v = 0; v < c->bn[g]; ++v)
             if (r[v + 1] - r[v] > kHeavyRow) heavy.push_back(v);
         c->bhoff[g + 1] = (int64_t)heavy.size();
         c->bheavy_n[g] = (int)(c->bhoff[g + 1] - c->bhoff[g]);
-        c->bblocks[g] = std::max(1, std::min<int>(c->num_sms * 2, (c->bn[g] + kSolveThreads - 1) / kSolveThreads));
-        max_parts = std::max(max_parts, c->bblocks[g] + c->bheavy_n[g]);
     }
-    c->solve_blocks = c->bblocks[0];
-    c->solve_n = max_n;
     if (cudaMalloc(&c->d_heavy, std::max<size_t>(1, heavy.size()) * 4) != cudaSuccess)
         return fail(c, UST_ENOMEM, "heavy rows");
     if (!heavy.empty())
         UST_CUDA_TRY(cudaMemcpyAsync(c->d_heavy, heavy.data(), heavy.size() * 4, cudaMemcpyHostToDevice, c->stream));
-    if (cudaMalloc(&c->d_f32, 5 * (size_t)max_n * sizeof(float)) != cudaSuccess)
-        return fail(c, UST_ENOMEM, "solver FP32 vectors");
-    if (cudaMalloc(&c->d_f64, 2 * (size_t)max_n * sizeof(double)) != cudaSuccess)
-        return fail(c, UST_ENOMEM, "solver FP64 vectors");
     if (cudaMalloc(&c->d_x, nv * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "columns");
-    const size_t parts = 8 * (size_t)max_parts + 8;
-    if (cudaMalloc(&c->d_red, parts * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver partials");
-    if (cudaMallocHost(&c->h_red, parts * sizeof(double)) != cudaSuccess)
-        return fail(c, UST_ENOMEM, "pinned solver partials");
+    if (cudaMalloc(&c->d_br64, nv * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver residuals");
+    if (cudaMalloc(&c->d_bw32, 5 * nv * sizeof(float)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver vectors");
+    if (cudaMalloc(&c->d_tasks, (size_t)B * sizeof(SolveTask)) != cudaSuccess) return fail(c, UST_ENOMEM, "tasks");
+    if (cudaMalloc(&c->d_results, (size_t)B * sizeof(SolveResult)) != cudaSuccess)
+        return fail(c, UST_ENOMEM, "solve results");
+    if (cudaMallocHost(&c->h_results, (size_t)B * sizeof(SolveResult)) != cudaSuccess)
+        return fail(c, UST_ENOMEM, "pinned solve results");
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return UST_OK;
 }

@@ -42,6 +42,32 @@ struct GraphDesc {
 // state in shared memory (4 bytes per vertex; ids below 2^16).
 constexpr int kSmemMaxVertices = 56 * 1024;
 
+// One sampler launch shape: threads per CTA (64, 128, 256, 512 or 1024) and
+// the persistent CTAs of the launch (a multiple of the SM count).
+struct LaunchCfg {
+    int bt = 0;
+    int ctas = 0;
+};
+
+// One linear system of the one-CTA column solve (see ust_solve_cta.cu).
+struct SolveTask {
+    int n = 0, u = 0;
+    const int32_t *rp = nullptr, *ci = nullptr;
+    const int32_t *heavy = nullptr;  // rows with more than kHeavyRow arcs
+    int n_heavy = 0;
+    double *x = nullptr;    // the column (output)
+    double *r64 = nullptr;  // n doubles of scratch
+    void *w = nullptr;      // 5 n scratch values of the inner precision
+};
+struct SolveResult {
+    int iters = 0, refinements = 0;
+    double relres = 0.0;
+};
+// Size classes of a batch: the graphs with at most kClassMaxN[k] vertices
+// (and more than the previous bound) share one sampler launch and shape.
+constexpr int kNumClasses = 6;
+constexpr int kClassMaxN[kNumClasses] = {4096, 8192, 14336, 28672, kSmemMaxVertices, 0x7FFFFFFF};
+
 // Per-CTA scratch of the sampling kernel: `kWsArrays` int32 arrays of
 // `stride` entries each, laid out array-major inside one CTA slot (the last
 // two form one 64-bit array).
@@ -85,10 +111,12 @@ struct Ctx {
     int64_t path_cap = 0;
 
     // sampling
-    int block_threads = 0, ctas = 0;
-    int64_t ws_stride = 0;
-    int32_t *d_ws = nullptr;    // ctas * kWsArrays * ws_stride
-    int32_t *d_Rp = nullptr;    // ctas * n partial counts
+    LaunchCfg cfg;                  // single graph: the sampler's launch shape
+    int req_bt = 0, req_cps = 0;    // requested threads per CTA / CTAs per SM (0 = automatic)
+    int64_t ws_stride = 0;          // single graph: words per workspace array
+    int64_t ws_cap = 0, rp_cap = 0; // capacity in int32 words of d_ws and d_Rp
+    int32_t *d_ws = nullptr;    // ctas * kWsArrays * stride
+    int32_t *d_Rp = nullptr;    // ctas * n partial counts (single graph)
     int64_t *d_R = nullptr;     // committed counts
     int64_t *d_Rtmp = nullptr;  // scratch counts (uncommitted)
     int64_t *d_stats = nullptr; // [0] draws, [1] rounds, [2] max rounds, [3] max depth, [4] next tree, [5] status
@@ -107,11 +135,17 @@ struct Ctx {
     int solve_blocks = 0;
     int32_t *d_heavy = nullptr;  // rows summed by a whole CTA in the SpMVs
     int n_heavy = 0;
+    SolveTask *d_tasks = nullptr;       // one-CTA solve: one task per graph
+    SolveResult *d_results = nullptr, *h_results = nullptr;
+    float *d_bw32 = nullptr;            // batch: 5 n floats of inner scratch (all graphs)
+    double *d_bw64 = nullptr;           // batch: 5 n doubles, FP64 inner scratch (on first use)
+    double *d_br64 = nullptr;           // batch: n doubles of residual scratch
 
     // phase timers: event pairs for bfs, sample kernel, reduce, solve, combine
     enum { kEvBfs = 0, kEvSample = 1, kEvReduce = 2, kEvSolve = 3, kEvCombine = 4, kEvPhases = 5 };
     cudaEvent_t ev[2 * kEvPhases] = {};
     bool ev_used[kEvPhases] = {};
+    bool ev_hold[kEvPhases] = {};
     int64_t launches = 0;
     int64_t last_trees = 0, last_draws = 0;
     int64_t last_phase_cycles[12] = {};
@@ -128,7 +162,9 @@ struct Ctx {
     // arrays one after another, graph g starting at bvoff[g]; row_ptr and
     // pathptr hold n_g + 1 entries per graph, starting at bvoff[g] + g.
     int batch = 0;
-    int ws_n = 0;  // vertices the sampler workspace is sized for (largest graph)
+    std::vector<int> bclass;              // size class of every graph
+    int class_maxn[kNumClasses] = {};     // largest graph of every class (0 = empty)
+    LaunchCfg class_cfg[kNumClasses];     // launch shape of every class
     std::vector<int> bn, bnnz, bpivot, becc, bheavy_n, bblocks;
     std::vector<int64_t> bvoff, baoff, bpoff, bhoff, btrees, bfarness;
     GraphDesc *d_graphs = nullptr;  // sampler descriptors (one for a single graph)
@@ -145,25 +181,51 @@ struct Ctx {
 int fail(Ctx *c, int code, const std::string &msg);
 
 // Records the start / end event of a timed phase on the context's stream.
-inline void phase_begin(Ctx *c, int ph) { cudaEventRecord(c->ev[2 * ph], c->stream); }
+// While a phase is held open (phase_open ... phase_close around several
+// launches), the inner begin / end pairs record nothing.
+inline void phase_begin(Ctx *c, int ph)
+{
+    if (!c->ev_hold[ph]) cudaEventRecord(c->ev[2 * ph], c->stream);
+}
 inline void phase_end(Ctx *c, int ph)
 {
+    if (c->ev_hold[ph]) return;
     cudaEventRecord(c->ev[2 * ph + 1], c->stream);
     c->ev_used[ph] = true;
+}
+inline void phase_open(Ctx *c, int ph)
+{
+    phase_begin(c, ph);
+    c->ev_hold[ph] = true;
+}
+inline void phase_close(Ctx *c, int ph)
+{
+    c->ev_hold[ph] = false;
+    phase_end(c, ph);
 }
 
 // Host drivers (one per translation unit).
 int run_bfs(Ctx *c);
+// Chooses the single-graph launch shape (requested or automatic) and sizes
+// the workspace for it.
 int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm);
+// The same for every size class of a batch.
+int alloc_batch_sampler(Ctx *c, int block_threads, int ctas_per_sm);
 // mode 0: aggregate trees [t0, t1) into d_out (int64 n) - added, not assigned.
 // mode 1: export next/pops of trees [t0, t1) to device buffers.
 int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
                 int32_t *d_pops_out, int64_t *draws, int64_t *rounds, int *max_rounds, int *max_depth);
 int run_batch_prepare(Ctx *c, const PrepDesc *d_desc, int count, int *d_out);
 int run_batch_combine(Ctx *c, const CombineDesc *d_desc, int count, double *d_diag);
-int run_batch_sampler(Ctx *c, const GraphDesc *d_graphs, const long long *d_item_start, int ngraphs,
-                      long long total_items, int max_n, long long max_rounds, uint64_t seed, int64_t *d_R,
-                      int64_t *draws, int64_t *rounds, int *max_round_count, int *max_pops);
+int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, const long long *d_item_start,
+                      int ngraphs, long long total_items, int max_n, long long max_rounds, uint64_t seed,
+                      int64_t *d_R, int64_t *draws, int64_t *rounds, int *max_round_count, int *max_pops);
+
+// Single graphs with at most this many arcs solve with one CTA; larger ones
+// with the multi-kernel solver. Batches always use one CTA per graph.
+constexpr int64_t kCtaSolveMaxArcs = 1 << 18;
+int run_solve_cta(Ctx *c, const SolveTask *d_tasks, int count, SolveResult *d_results, SolveResult *h_results,
+                  bool fp64);
 
 // One graph's column solve: the scratch vectors of the context are sized for
 // solve_n >= n vertices.

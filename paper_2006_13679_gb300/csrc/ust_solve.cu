@@ -328,6 +328,10 @@ int alloc_solver(Ctx *c)
     if (!heavy.empty())
         UST_CUDA_TRY(cudaMemcpyAsync(c->d_heavy, heavy.data(), heavy.size() * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, c->stream));
+    if (cudaMalloc(&c->d_tasks, sizeof(SolveTask)) != cudaSuccess) return fail(c, UST_ENOMEM, "solve task");
+    if (cudaMalloc(&c->d_results, sizeof(SolveResult)) != cudaSuccess) return fail(c, UST_ENOMEM, "solve result");
+    if (cudaMallocHost(&c->h_results, sizeof(SolveResult)) != cudaSuccess)
+        return fail(c, UST_ENOMEM, "pinned solve result");
     const size_t parts = 8 * ((size_t)c->solve_blocks + (size_t)c->n_heavy) + 8;
     if (cudaMalloc(&c->d_f32, 5 * n * sizeof(float)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver FP32 vectors");
     if (cudaMalloc(&c->d_f64, 2 * n * sizeof(double)) != cudaSuccess) return fail(c, UST_ENOMEM, "solver FP64 vectors");
@@ -441,6 +445,28 @@ int run_solve_view(Ctx *c, const SolveView &g)
 
 int run_solve(Ctx *c)
 {
+    if ((int64_t)c->nnz <= kCtaSolveMaxArcs) {
+        // one CTA, one launch: the FP64 residual lives in d_f64, the inner
+        // vectors in d_f32 (or d_f64inner for the all-FP64 form)
+        if (c->solve_fp64 && !c->d_f64inner) {
+            if (cudaMalloc(&c->d_f64inner, 5 * (size_t)c->solve_n * sizeof(double)) != cudaSuccess)
+                return fail(c, UST_ENOMEM, "FP64 solver vectors");
+        }
+        SolveTask t;
+        t.n = c->n;
+        t.u = c->pivot;
+        t.rp = c->d_rp;
+        t.ci = c->d_ci;
+        t.heavy = c->d_heavy;
+        t.n_heavy = c->n_heavy;
+        t.x = c->d_x;
+        t.r64 = c->d_f64;
+        t.w = c->solve_fp64 ? (void *)c->d_f64inner : (void *)c->d_f32;
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_tasks, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
+        const int rc = run_solve_cta(c, c->d_tasks, 1, c->d_results, c->h_results, c->solve_fp64);
+        if (rc == UST_OK) c->x_valid = true;
+        return rc;
+    }
     SolveView g;
     g.n = c->n;
     g.u = c->pivot;

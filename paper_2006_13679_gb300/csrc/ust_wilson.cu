@@ -1181,36 +1181,149 @@ __global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict_
 // 2^16 so that two 16-bit halves fit one word).
 constexpr int kSmemMaxN = kSmemMaxVertices;
 
+size_t smem_bytes_for(int max_n) { return (size_t)((max_n + 1) / 2) * 2 * sizeof(uint32_t); }
+
+int64_t stride_for(int max_n) { return ((int64_t)max_n + 2 + 31) / 32 * 32; }
+
+// Graphs above kSmemMaxN run the global-memory kernel, built for 256 threads
+// and more; graphs within it run the shared-memory kernel at any shape.
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
     if (p.max_n <= kSmemMaxN) {
-        const size_t bytes = (size_t)((p.max_n + 1) / 2) * 2 * sizeof(uint32_t);
+        const size_t bytes = smem_bytes_for(p.max_n);
         cudaError_t e = cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         sample_aggregate_smem_kernel<BT><<<grid, BT, bytes, st>>>(p);
     } else {
-        sample_aggregate_kernel<BT, false><<<grid, BT, 0, st>>>(p);
+        if constexpr (BT >= 256)
+            sample_aggregate_kernel<BT, false><<<grid, BT, 0, st>>>(p);
+        else
+            return cudaErrorInvalidConfiguration;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_shape(const LaunchCfg &cfg, int grid, cudaStream_t st, const SampleParams &p)
+{
+    switch (cfg.bt) {
+    case 64: return launch_sampler<64>(grid, st, p);
+    case 128: return launch_sampler<128>(grid, st, p);
+    case 256: return launch_sampler<256>(grid, st, p);
+    case 512: return launch_sampler<512>(grid, st, p);
+    case 1024: return launch_sampler<1024>(grid, st, p);
+    default: return cudaErrorInvalidConfiguration;
+    }
+}
+
+// Resident CTAs per SM of the kernel that serves graphs of max_n vertices at
+// BT threads (registers, shared memory and the SM's thread limit together).
+template <int BT>
+int resident_ctas(int max_n)
+{
+    int blocks = 0;
+    if (max_n <= kSmemMaxN) {
+        const size_t bytes = smem_bytes_for(max_n);
+        if (cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_smem_kernel<BT>, BT, bytes) !=
+            cudaSuccess)
+            return 0;
+    } else {
+        if constexpr (BT >= 256) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_kernel<BT, false>, BT, 0) !=
+                cudaSuccess)
+                return 0;
+        }
+    }
+    return blocks;
+}
+
+int resident_ctas_for(int bt, int max_n)
+{
+    switch (bt) {
+    case 64: return resident_ctas<64>(max_n);
+    case 128: return resident_ctas<128>(max_n);
+    case 256: return resident_ctas<256>(max_n);
+    case 512: return resident_ctas<512>(max_n);
+    case 1024: return resident_ctas<1024>(max_n);
+    default: return 0;
+    }
+}
+
+// Automatic threads per CTA: small trees get small CTAs (more trees in
+// flight per SM, cheaper barriers), large ones a whole SM.
+int default_bt(int max_n)
+{
+    if (max_n <= 8192) return 128;
+    if (max_n <= 14336) return 256;
+    if (max_n <= 28672) return 512;
+    if (max_n <= kSmemMaxN) return 1024;
+    return 512;
+}
+
+bool valid_bt(int bt) { return bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
+
+int choose_cfg(Ctx *c, int max_n, int req_bt, int req_cps, LaunchCfg *out)
+{
+    int bt = valid_bt(req_bt) ? req_bt : default_bt(max_n);
+    if (max_n > kSmemMaxN && bt < 256) bt = 256;
+    const int resident = resident_ctas_for(bt, max_n);
+    if (resident < 1) return fail(c, UST_EINVAL, "no sampler launch shape fits this graph at the requested threads");
+    const int cps = req_cps > 0 ? std::min(req_cps, resident) : resident;
+    out->bt = bt;
+    out->ctas = c->num_sms * cps;
+    return UST_OK;
+}
+
+// Grows the workspace and partial-count arrays to at least these sizes.
+int reserve_workspace(Ctx *c, int64_t ws_words, int64_t rp_words)
+{
+    if (ws_words > c->ws_cap) {
+        cudaFree(c->d_ws);
+        c->d_ws = nullptr;
+        c->ws_cap = 0;
+        if (cudaMalloc(&c->d_ws, (size_t)ws_words * sizeof(int32_t)) != cudaSuccess)
+            return fail(c, UST_ENOMEM, "sampler workspace");
+        c->ws_cap = ws_words;
+    }
+    if (rp_words > c->rp_cap) {
+        cudaFree(c->d_Rp);
+        c->d_Rp = nullptr;
+        c->rp_cap = 0;
+        if (cudaMalloc(&c->d_Rp, (size_t)rp_words * sizeof(int32_t)) != cudaSuccess)
+            return fail(c, UST_ENOMEM, "partial counts");
+        c->rp_cap = rp_words;
+    }
+    return UST_OK;
 }
 
 }  // namespace
 
 int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm)
 {
-    if (block_threads != 256 && block_threads != 512 && block_threads != 1024) block_threads = 1024;
-    if (ctas_per_sm < 1) ctas_per_sm = (block_threads == 1024) ? 1 : 1024 / block_threads;
-    c->block_threads = block_threads;
-    c->ctas = c->num_sms * ctas_per_sm;
-    const int64_t nw = c->ws_n > 0 ? c->ws_n : c->n;  // a batch sizes it for its largest graph
-    c->ws_stride = (nw + 2 + 31) / 32 * 32;
-    const size_t ws_bytes = (size_t)c->ctas * kWsArrays * (size_t)c->ws_stride * sizeof(int32_t);
-    const size_t rp_bytes = (size_t)c->ctas * (size_t)nw * sizeof(int32_t);
-    if (cudaMalloc(&c->d_ws, ws_bytes) != cudaSuccess) return fail(c, UST_ENOMEM, "sampler workspace");
-    if (cudaMalloc(&c->d_Rp, rp_bytes) != cudaSuccess) return fail(c, UST_ENOMEM, "partial counts");
-    return UST_OK;
+    c->req_bt = block_threads;
+    c->req_cps = ctas_per_sm;
+    int rc = choose_cfg(c, c->n, block_threads, ctas_per_sm, &c->cfg);
+    if (rc) return rc;
+    c->ws_stride = stride_for(c->n);
+    return reserve_workspace(c, (int64_t)c->cfg.ctas * kWsArrays * c->ws_stride, (int64_t)c->cfg.ctas * c->n);
+}
+
+int alloc_batch_sampler(Ctx *c, int block_threads, int ctas_per_sm)
+{
+    c->req_bt = block_threads;
+    c->req_cps = ctas_per_sm;
+    int64_t ws = 0;
+    for (int k = 0; k < kNumClasses; ++k) {
+        if (c->class_maxn[k] <= 0) continue;
+        const int rc = choose_cfg(c, c->class_maxn[k], block_threads, ctas_per_sm, &c->class_cfg[k]);
+        if (rc) return rc;
+        ws = std::max<int64_t>(ws, (int64_t)c->class_cfg[k].ctas * kWsArrays * stride_for(c->class_maxn[k]));
+    }
+    return reserve_workspace(c, ws, 0);
 }
 
 int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
@@ -1219,7 +1332,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     if (t1 <= t0) return UST_OK;
     if (t0 < 0 || t1 > (int64_t)0xFFFFFFFFll) return fail(c, UST_EINVAL, "tree ids must lie in [0, 2^32)");
     const int mode = d_next_out ? 1 : 0;
-    const int grid = (int)std::min<int64_t>(c->ctas, t1 - t0);
+    const int grid = (int)std::min<int64_t>(c->cfg.ctas, t1 - t0);
     if (mode == 0)
         UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
     UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
@@ -1277,13 +1390,8 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     p.next_out = d_next_out;
     p.pops_out = d_pops_out;
 
-    cudaError_t e;
     phase_begin(c, Ctx::kEvSample);
-    switch (c->block_threads) {
-    case 256: e = launch_sampler<256>(grid, c->stream, p); break;
-    case 1024: e = launch_sampler<1024>(grid, c->stream, p); break;
-    default: e = launch_sampler<512>(grid, c->stream, p); break;
-    }
+    const cudaError_t e = launch_shape(c->cfg, grid, c->stream, p);
     phase_end(c, Ctx::kEvSample);
     c->launches += 1;
     if (e != cudaSuccess) return fail(c, UST_ECUDA, std::string("sampler launch: ") + cudaGetErrorString(e));
@@ -1610,9 +1718,9 @@ int run_batch_combine(Ctx *c, const CombineDesc *d_desc, int count, double *d_di
     return UST_OK;
 }
 
-int run_batch_sampler(Ctx *c, const GraphDesc *d_graphs, const long long *d_item_start, int ngraphs,
-                      long long total_items, int max_n, long long max_rounds, uint64_t seed, int64_t *d_R,
-                      int64_t *draws, int64_t *rounds, int *max_round_count, int *max_pops)
+int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, const long long *d_item_start,
+                      int ngraphs, long long total_items, int max_n, long long max_rounds, uint64_t seed,
+                      int64_t *d_R, int64_t *draws, int64_t *rounds, int *max_round_count, int *max_pops)
 {
     if (total_items <= 0) return UST_OK;
     UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
@@ -1621,9 +1729,11 @@ int run_batch_sampler(Ctx *c, const GraphDesc *d_graphs, const long long *d_item
     p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
     p.key1 = (uint32_t)(seed >> 32);
     p.ws = c->d_ws;
-    p.stride = c->ws_stride;
+    p.stride = stride_for(max_n);
     p.Rp = c->d_Rp;
     p.tree_offset = 0;
+    if ((int64_t)std::min<long long>(cfg.ctas, total_items) * kWsArrays * p.stride > c->ws_cap)
+        return fail(c, UST_ECUDA, "batch sampler: workspace smaller than the launch needs");
     unsigned long long *st = reinterpret_cast<unsigned long long *>(c->d_stats);
     p.next_tree = st + 4;
     p.stats = st;
@@ -1638,14 +1748,9 @@ int run_batch_sampler(Ctx *c, const GraphDesc *d_graphs, const long long *d_item
     p.item_start = d_item_start;
     p.total_items = total_items;
     p.R_direct = reinterpret_cast<unsigned long long *>(d_R);
-    const int grid = (int)std::min<long long>(c->ctas, total_items);
-    cudaError_t e;
+    const int grid = (int)std::min<long long>(cfg.ctas, total_items);
     phase_begin(c, Ctx::kEvSample);
-    switch (c->block_threads) {
-    case 256: e = launch_sampler<256>(grid, c->stream, p); break;
-    case 1024: e = launch_sampler<1024>(grid, c->stream, p); break;
-    default: e = launch_sampler<512>(grid, c->stream, p); break;
-    }
+    const cudaError_t e = launch_shape(cfg, grid, c->stream, p);
     phase_end(c, Ctx::kEvSample);
     c->launches += 1;
     if (e != cudaSuccess) return fail(c, UST_ECUDA, std::string("batch sampler launch: ") + cudaGetErrorString(e));
