@@ -152,6 +152,10 @@ __device__ __forceinline__ int classify_node(const int32_t *Sx, int i, int limit
     return 0;
 }
 
+// Vertices a popping-round walk passes before it starts marking them for
+// other walks (short walks skip the bookkeeping).
+constexpr int kQuietSteps = 0;
+
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
 constexpr int kPathChunk = 4;
@@ -174,6 +178,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // redrawn vertices of this / next round
     int32_t *Sx = base + 6 * S_;      // S(x) as an index into the round's list, -1 = reaches u
     int32_t *J0 = base + 7 * S_;   // with base + 8 * S_: packed 64-bit words (queue, preorder)
+    int32_t *owner = J0, *wlen = base + 8 * S_;  // during the popping rounds (see below)
     int32_t *L0 = base + 9 * S_;   // leaf queue of the peeling
     // children bookkeeping: high word = children not yet finished (the
     // children count while sampling), low word = summed subtree sizes
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
     constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err, s_abort, s_qn, s_qh;
+    __shared__ int s_cnt, s_err, s_abort, s_qn, s_qh, s_linked;
     __shared__ unsigned long long s_root_sum;  // the root's children: summed subtree sizes
     __shared__ unsigned long long s_draws;
     __shared__ unsigned long long cyc[8];  // clock64 per phase, kept by thread 0
@@ -366,48 +371,82 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
             if (tid == 0) {
                 s_draws += (unsigned long long)nX;
                 s_cnt = 0;
+                s_linked = 0;
                 my_max_pops = max(my_max_pops, nX);
             }
             __syncthreads();
-            // (b) S(x): first redrawn vertex or known-final vertex after x
+            // (b) S(x): first redrawn vertex or known-final vertex after x;
+            //     a walk that reaches a vertex another walk of this round
+            //     passed (mark -2 - rounds) stops and takes that walk's
+            //     result, resolved after the barrier (as in the
+            //     shared-memory kernel)
+            const int vis = -2 - rounds;
             for (int i = tid; i < nX; i += BT) {
                 int y = nxt[X[i]];
-                int res = -2;
+                int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = rmark[y];
                     const int ny = nxt[y];
                     if (m == kFinal) { res = -1; break; }
                     if (m == rounds) { res = pos[y]; break; }
+                    if (m == vis) {
+                        __threadfence_block();
+                        res = -3 - owner[y];
+                        s_linked = 1;
+                        break;
+                    }
+                    if (len >= kQuietSteps) {  // short walks skip the bookkeeping
+                        owner[y] = i;
+                        __threadfence_block();  // the owner is visible before the mark
+                        rmark[y] = vis;
+                    }
+                    ++len;
                     y = ny;
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
+                wlen[i] = len;
             }
             __syncthreads();
-            // (c) nodes that reach -1 mark their segment final; nodes on a
-            //     cycle of i -> S(i) queue their segment for popping
+            if (s_linked) {  // some walk stopped on another's path: resolve the links
+                for (int i = tid; i < nX; i += BT) {
+                    int r = Sx[i];
+                    for (int guard = 0; r <= -3 && guard <= nX; ++guard) {
+                        const int j = -3 - r;
+                        if (j >= nX) break;  // not a walk of this round: reported below
+                        r = Sx[j];
+                    }
+                    if (r <= -3 || r >= nX) { s_err = 1; r = -1; }
+                    Sx[i] = r;
+                }
+                __syncthreads();
+            }
+            // (c) nodes that reach -1 mark x and their own walked part final;
+            //     nodes on a cycle of i -> S(i) queue their whole segment for
+            //     popping
             for (int i = tid; i < nX; i += BT) {
                 const int kind = classify_node(Sx, i, nX);
                 int y = X[i];
                 if (kind == 1) {
-                    for (int guard = 0; guard <= n; ++guard) {
-                        rmark[y] = kFinal;
+                    const int len = wlen[i];
+                    rmark[y] = kFinal;
+                    for (int k = 0; k < len; ++k) {
                         y = nxt[y];
-                        const int m = rmark[y];
-                        if (m == kFinal || m == rounds) break;
+                        rmark[y] = kFinal;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
-                        Xn[atomicAdd(&s_cnt, 1)] = y;
-                        y = nxt[y];
+                        Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
+                        y = max(nxt[y], 0);  // nxt[u] = -1: an inconsistent walk stays in the array
                         if (rmark[y] == rounds) break;
                     }
+                    if (rmark[y] != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
                 }
             }
             __syncthreads();
             nX = s_cnt;
             int32_t *tmp = X; X = Xn; Xn = tmp;
-            if (s_err) {
+            if (s_err || nX > n) {
                 failed = true;
                 if (tid == 0) atomicOr(p.status, kStatusBadState);
                 break;
@@ -678,7 +717,11 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
 // neighbour and are updated by adding or subtracting 1 << 16 * (v & 1); a
 // count never passes below 0 or above n - 1, so halves never carry.
 constexpr uint16_t kFinal16 = 0xFFFFu;
-constexpr int kMaxStamp16 = 0xFFFE;
+// Round marks: the round's stamp s in [1, kMaxStamp15] on redrawn vertices,
+// s | kVisited16 on the vertices a walk of round s passed, kFinal16 on
+// vertices known to reach u.
+constexpr int kMaxStamp15 = 0x7FFE;
+constexpr uint16_t kVisited16 = 0x8000u;
 
 __device__ __forceinline__ uint32_t half_add(uint32_t *words, int v, int delta)
 {
@@ -703,12 +746,14 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
     int32_t *pos = base + 3 * S_;     // index of a redrawn vertex in the round's list
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;
     int32_t *Sx = base + 6 * S_;
+    int32_t *owner = base + 7 * S_;   // the walk of this round that passed a vertex
+    int32_t *wlen = base + 8 * S_;    // vertices a walk passed before it stopped
     int32_t *off = XA;
     int32_t *Rp = p.Rp + (long long)blockIdx.x * p.max_n;
     constexpr uint32_t kC16 = 1u << 16;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err, s_qn, s_qh;
+    __shared__ int s_cnt, s_err, s_qn, s_qh, s_linked;
     __shared__ unsigned long long s_draws;
     __shared__ unsigned long long cyc[12];
     __shared__ long long tmark;
@@ -762,7 +807,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 if (v < n) {
                     pop[v] = 0;
                     nxt[v] = y[k];
-                    nx16[v] = (uint16_t)y[k];
+                    nx16[v] = (uint16_t)(v == u ? u : y[k]);  // u points at itself: no walk leaves the array
                 }
             }
         }
@@ -850,7 +895,8 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 if (tid == 0) atomicOr(p.status, kStatusPopRounds);
                 break;
             }
-            const int stamp = (rounds - 1) % kMaxStamp16 + 1;
+            const int stamp = (rounds - 1) % kMaxStamp15 + 1;
+            const int vis = stamp | kVisited16;
             if (stamp == 1 && rounds > 1) {  // stamps wrap: forget old ones
                 for (int v = tid; v < n; v += BT)
                     if (lo16[v] != kFinal16) lo16[v] = 0;
@@ -870,48 +916,87 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             if (tid == 0) {
                 s_draws += (unsigned long long)nX;
                 s_cnt = 0;
+                s_linked = 0;
                 my_max_pops = max(my_max_pops, nX);
             }
             __syncthreads();
-            // (b) S(x): first redrawn vertex or known-final vertex after x
+            // (b) S(x): first redrawn vertex or known-final vertex after x.
+            //     A walk that reaches a vertex another walk of this round
+            //     already passed stops there and takes that walk's result
+            //     (the two paths coincide from there on); the links are
+            //     resolved after the barrier. Links cannot form a cycle: every
+            //     cycle of this round passes a redrawn vertex.
+            //     A walk publishes the owner of a vertex before its mark
+            //     (block fence), so a walk that sees the mark reads the
+            //     owner of this round. The first kQuietSteps vertices of a
+            //     walk are not marked: short walks skip the bookkeeping.
             for (int i = tid; i < nX; i += BT) {
                 int y = nx16[X[i]];
-                int res = -2;
+                int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = lo16[y];
                     if (m == kFinal16) { res = -1; break; }
                     if (m == stamp) { res = pos[y]; break; }
+                    if (m == vis) {
+                        __threadfence_block();
+                        res = -3 - owner[y];
+                        s_linked = 1;
+                        break;
+                    }
+                    if (len >= kQuietSteps) {
+                        owner[y] = i;
+                        __threadfence_block();
+                        lo16[y] = (uint16_t)vis;
+                    }
+                    ++len;
                     y = nx16[y];
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
+                wlen[i] = len;
             }
             __syncthreads();
-            // (c) nodes that reach -1 mark their segment final; nodes on a
-            //     cycle of i -> S(i) queue their segment (x up to S(x)) for
-            //     popping; the other nodes keep their stack tops.
+            if (s_linked) {  // some walk stopped on another's path: resolve the links
+                for (int i = tid; i < nX; i += BT) {
+                    int r = Sx[i];
+                    for (int guard = 0; r <= -3 && guard <= nX; ++guard) {
+                        const int j = -3 - r;
+                        if (j >= nX) break;  // not a walk of this round: reported below
+                        r = Sx[j];
+                    }
+                    if (r <= -3 || r >= nX) { s_err = 1; r = -1; }
+                    Sx[i] = r;  // a reader sees the link or its result: both lead to the same end
+                }
+                __syncthreads();
+            }
+            // (c) nodes that reach -1 mark x and their own walked part final
+            //     (a linked walk's remainder is marked by its owner, which
+            //     reaches -1 too); nodes on a cycle of i -> S(i) queue their
+            //     whole segment (x up to S(x)) for popping; the other nodes
+            //     keep their stack tops.
             for (int i = tid; i < nX; i += BT) {
                 const int kind = classify_node(Sx, i, nX);
                 int y = X[i];
                 if (kind == 1) {
-                    for (int guard = 0; guard <= n; ++guard) {
-                        lo16[y] = kFinal16;
+                    const int len = wlen[i];
+                    lo16[y] = kFinal16;
+                    for (int k = 0; k < len; ++k) {
                         y = nx16[y];
-                        const int m = lo16[y];
-                        if (m == kFinal16 || m == stamp) break;
+                        lo16[y] = kFinal16;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
-                        Xn[atomicAdd(&s_cnt, 1)] = y;
+                        Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
                         y = nx16[y];
                         if (lo16[y] == stamp) break;
                     }
+                    if (lo16[y] != stamp) s_err = 1;  // a cycle segment ends at a redrawn vertex
                 }
             }
             __syncthreads();
             nX = s_cnt;
             int32_t *tmp = X; X = Xn; Xn = tmp;
-            if (s_err) {
+            if (s_err || nX > n) {
                 failed = true;
                 if (tid == 0) atomicOr(p.status, kStatusBadState);
                 break;
