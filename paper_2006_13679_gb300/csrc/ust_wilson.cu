@@ -155,6 +155,9 @@ __device__ __forceinline__ int classify_node(const int32_t *Sx, int i, int limit
 // Vertices a popping-round walk passes before it starts marking them for
 // other walks (short walks skip the bookkeeping).
 constexpr int kQuietSteps = 0;
+// The shared-memory kernel marks paths only in rounds after one whose longest
+// walk exceeded this many steps (short walks gain nothing from the stops).
+constexpr int kMarkMinWalk = 32;
 
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
@@ -753,7 +756,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
     constexpr uint32_t kC16 = 1u << 16;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err, s_qn, s_qh, s_linked;
+    __shared__ int s_cnt, s_err, s_qn, s_qh, s_linked, s_mark_on, s_maxwalk;
     __shared__ unsigned long long s_draws;
     __shared__ unsigned long long cyc[12];
     __shared__ long long tmark;
@@ -881,6 +884,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         }
         __syncthreads();
         for (int v = tid; v < n; v += BT) lo16[v] = (v == u) ? kFinal16 : 0;  // round marks
+        if (tid == 0) s_maxwalk = 0;
         __syncthreads();
         UST_PHASE(4);
         int nX = s_cnt;
@@ -917,6 +921,9 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 s_draws += (unsigned long long)nX;
                 s_cnt = 0;
                 s_linked = 0;
+                // mark paths for other walks only while walks are long
+                s_mark_on = (rounds == 1) || (s_maxwalk > kMarkMinWalk);
+                s_maxwalk = 0;
                 my_max_pops = max(my_max_pops, nX);
             }
             __syncthreads();
@@ -930,6 +937,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
             //     (block fence), so a walk that sees the mark reads the
             //     owner of this round. The first kQuietSteps vertices of a
             //     walk are not marked: short walks skip the bookkeeping.
+            const bool mark_on = s_mark_on;
             for (int i = tid; i < nX; i += BT) {
                 int y = nx16[X[i]];
                 int res = -2, len = 0;
@@ -943,7 +951,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                         s_linked = 1;
                         break;
                     }
-                    if (len >= kQuietSteps) {
+                    if (mark_on && len >= kQuietSteps) {
                         owner[y] = i;
                         __threadfence_block();
                         lo16[y] = (uint16_t)vis;
@@ -954,6 +962,7 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
                 wlen[i] = len;
+                atomicMax(&s_maxwalk, len);
             }
             __syncthreads();
             if (s_linked) {  // some walk stopped on another's path: resolve the links
@@ -1346,7 +1355,9 @@ int default_bt(int max_n)
     if (max_n <= 14336) return 256;
     if (max_n <= 28672) return 512;
     if (max_n <= kSmemMaxN) return 1024;
-    return 512;
+    // above the shared-memory sampler: two trees per SM while the per-tree
+    // arrays are small, one whole-SM tree per SM for the very large graphs
+    return max_n <= 262144 ? 512 : 1024;
 }
 
 bool valid_bt(int bt) { return bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
