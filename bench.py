@@ -10,9 +10,10 @@ write) between timed steps, outside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line. With N > 1 (torchrun, one rank per GPU) every rank
-samples its own 4096 trees (seed offset by rank; weak scaling), the integer
-counts are summed across ranks (the paper's final reduction of R) and the
+Prints one JSON line. With N > 1 (torchrun, one rank per GPU) rank r
+samples the tree ids [4096 r, 4096 (r + 1)) under the common seed (weak
+scaling), the integer counts are summed across ranks (the paper's final
+reduction of R; the sum equals one GPU sampling all 4096 N trees) and the
 max step time over ranks is reported.
 """
 from __future__ import annotations
@@ -264,11 +265,12 @@ def run_batch_gpu(args, rank: int, world: int, local_rank: int, dist) -> None:
 
     def step():
         b.reset()                     # B_u of every graph, clear R and columns
-        b.sample_aggregate(T, seed)   # T trees of every graph
-        if dist is not None:
+        b.sample_aggregate(T, seed)   # T trees of every graph (seed offset by rank)
+        if dist is not None:          # counts summed over ranks and installed
             b.counts(counts_d)
             with torch.cuda.stream(stream):
                 dist.all_reduce(counts_d)
+            b.set_counts(counts_d, world * T)
         b.diag(0.0, diag_d)           # every graph's column solve + combination
 
     for _ in range(args.warmup):
@@ -438,12 +440,13 @@ def main() -> None:
         dist.init_process_group("nccl")
 
     pkg.build()
+    from paper_2006_13679_gb300 import parallel
     if args.workload == "batch256":
         run_batch_gpu(args, rank, world, local_rank, dist)
         return
     g, u, T0, eps = synth.workload(args.workload)
     T = workload_trees(g, u, T0, eps)
-    seed = SEED + rank
+    seed = SEED
     stream = torch.cuda.Stream()
     rp_d = torch.from_numpy(g.row_ptr).cuda()
     ci_d = torch.from_numpy(g.col_idx).cuda()
@@ -454,11 +457,11 @@ def main() -> None:
 
     def step():
         h.reset(u)                    # B_u, ecc, clear R
-        h.sample_aggregate(T, seed)   # Wilson + intervals + Algorithm 2 + exact reduction
-        if dist is not None:          # the paper's final reduction of R over ranks
-            h.counts(counts_d)
+        if dist is None:
+            h.sample_aggregate(T, seed)   # Wilson + intervals + Algorithm 2 + exact reduction
+        else:                         # this rank's tree ids, counts summed over ranks and installed
             with torch.cuda.stream(stream):
-                dist.all_reduce(counts_d)
+                parallel.sample_sharded(h, T, seed, out=counts_d)
         h.diag(0.0, diag_d)           # column solve + combination
 
     for _ in range(args.warmup):
@@ -563,7 +566,7 @@ def main() -> None:
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; n={g.n} m={g.m}, "
-                                       f"pivot {u}, {T} trees per GPU, seed {SEED}+rank",
+                                       f"pivot {u}, {T} trees per GPU (tree ids rank*{T} onwards), seed {SEED}",
                            "l2": "flushed between timed steps (256 MB write)",
                            "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads"},
                 "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,

@@ -206,6 +206,20 @@ UST_API int ust_get_bfs(ust_ctx *c, int32_t *parent_out, int32_t *dist_out);
 UST_API int ust_tree_range_counts(ust_ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *R_out,
                           int32_t out_on_device);
 
+/* Replaces the context's R with R_in (n int64, exact Algorithm-2 counts of
+ * `trees` trees of this graph and pivot) and its tree count with `trees`.
+ * This is how counts sampled elsewhere are combined before ust_diag: the
+ * paper distributes trees over processes and sums R at the end (Appendix D,
+ * distributed-memory parallelism); here each GPU computes the counts of its
+ * own tree-id range with ust_tree_range_counts under a common seed, the
+ * integer rows are summed (an exact, order-free reduction), and the sum is
+ * installed with this call. The library cannot verify R_in. The cached
+ * column stays valid (it depends only on the graph and pivot). For a batch,
+ * R_in holds every graph's counts (offsets as ust_batch_offsets) and every
+ * graph gets `trees` trees. Errors: UST_EINVAL (NULL R_in, trees < 1),
+ * UST_ECUDA. */
+UST_API int ust_set_counts(ust_ctx *c, const int64_t *R_in, int64_t trees, int32_t in_on_device);
+
 /* The sampled trees themselves: for tree ids t0 .. t0+count-1 writes
  * next_out[i*n + v] (tree parent of v, -1 at u) and, when pops_out is not
  * NULL, pops_out[i*n + v] (cycles popped at v = stack depth of the final

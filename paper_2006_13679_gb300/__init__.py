@@ -152,6 +152,12 @@ class UST:
         check(load().ust_tree_range_counts(self._h, int(t0), int(t1), int(seed) & (2 ** 64 - 1), p, dev), self._h)
         return out
 
+    def set_counts(self, R, trees: int) -> None:
+        """Installs exact counts of `trees` trees (e.g. summed over GPUs) as R."""
+        R = R if _is_torch(R) else np.ascontiguousarray(R, dtype=np.int64)
+        ptr, dev = _ptr(R, np.int64)
+        check(load().ust_set_counts(self._h, ptr, int(trees), dev), self._h)
+
     def sample_trees(self, t0: int, count: int, seed: int, with_pops: bool = False):
         nxt = np.empty((count, self.n), dtype=np.int32)
         pops = np.empty((count, self.n), dtype=np.int32) if with_pops else None
@@ -216,6 +222,7 @@ class USTBatch:
     __enter__ = UST.__enter__
     __exit__ = UST.__exit__
     sample_aggregate = UST.sample_aggregate
+    set_counts = UST.set_counts
     tau = UST.tau
     _out = UST._out
     diag = UST.diag

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "ust_batch_graph_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ust_info)]),
     "ust_reset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "ust_sample_aggregate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]),
+    "ust_set_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
     "ust_diag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int32]),
     "ust_tau": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_double]),
     "ust_get_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),

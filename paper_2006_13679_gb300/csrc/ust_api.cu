@@ -393,6 +393,23 @@ int ust_tree_range_counts(ust_ctx *h, int64_t t0, int64_t t1, uint64_t seed, int
     return copy_out(c, R_out, c->d_Rtmp, (size_t)c->n * 8, out_on_device);
 }
 
+int ust_set_counts(ust_ctx *h, const int64_t *R_in, int64_t trees, int32_t in_on_device)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (!R_in || trees < 1) return ust::fail(c, UST_EINVAL, "ust_set_counts needs counts and trees >= 1");
+    UST_CUDA_TRY(cudaMemcpyAsync(c->d_R, R_in, (size_t)c->n * 8,
+                                 in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->batch) {  // every graph of the batch gets `trees` trees
+        for (int g = 0; g < c->batch; ++g) c->btrees[g] = trees;
+        c->trees = trees * c->batch;
+    } else {
+        c->trees = trees;
+    }
+    return UST_OK;
+}
+
 int ust_sample_trees(ust_ctx *h, int64_t t0, int32_t count, uint64_t seed, int32_t *next_out, int32_t *pops_out)
 {
     if (!h) return UST_EINVAL;

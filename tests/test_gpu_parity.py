@@ -276,3 +276,22 @@ def test_one_tree_per_launch_equals_batched(pkg, orc):
         for _ in range(64):
             b.sample_aggregate(1, 5)
         assert np.array_equal(a.counts(), b.counts())
+
+
+def test_sharded_tree_ranges_equal_one_run(pkg, orc):
+    """Two ranks' tree ranges under one seed, summed and installed with
+    ust_set_counts, give the counts and diagonal of one context that sampled
+    all the trees (the multi-GPU path, emulated in one process)."""
+    from paper_2006_13679_gb300 import parallel
+    g, u = synth.rmat(12, 16, seed=5), None
+    u = synth.max_degree_vertex(g)
+    T = 300
+    with pkg.UST(g.row_ptr, g.col_idx, u) as h1, pkg.UST(g.row_ptr, g.col_idx, u) as h2:
+        h1.sample_aggregate(2 * T, 5)
+        R = sum(h2.tree_range_counts(*parallel.tree_range(r, 2, T), 5) for r in range(2))
+        h2.set_counts(R, 2 * T)
+        assert np.array_equal(h2.counts(), h1.counts())
+        assert h2.info()["trees"] == 2 * T
+        np.testing.assert_array_equal(h2.diag(), h1.diag())
+        with pytest.raises(pkg.UstError):
+            h2.set_counts(R, 0)
