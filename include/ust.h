@@ -244,7 +244,7 @@ UST_API int ust_get_info(const ust_ctx *c, ust_info *out);
  * stream is a cudaStream_t or NULL; the call synchronises it before returning.
  *
  * All scratch lives in one fixed device array inside the library (about
- * 8.5 MB, held on every GPU that loads the library until the process exits).
+ * 10.6 MB, held on every GPU that loads the library until the process exits).
  * Limits: n <= 4096 and f^c(u) = sum_v dist(u, v) <= 262144; larger inputs
  * return UST_EINVAL before any work. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;

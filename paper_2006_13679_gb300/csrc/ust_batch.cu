@@ -44,6 +44,9 @@ GraphDesc desc_of(const Ctx *c, int g, long long tree_begin)
     d.bpar = c->d_bpar + c->bvoff[g];
     d.path = c->d_path + c->bpoff[g];
     d.pathptr = c->d_pathptr + c->bvoff[g] + g;
+    d.pchild = c->d_path + c->path_cap + c->bpoff[g];
+    d.powner = c->d_path + 2 * c->path_cap + c->bpoff[g];
+    d.fc = (int)c->bfarness[g];
     return d;
 }
 
@@ -64,6 +67,8 @@ int batch_prepare(Ctx *c, bool fill)
         d.bpar = c->d_bpar + c->bvoff[g];
         d.pathptr = c->d_pathptr + c->bvoff[g] + g;
         d.path = fill ? c->d_path + c->bpoff[g] : nullptr;
+        d.pchild = fill ? c->d_path + c->path_cap + c->bpoff[g] : nullptr;
+        d.powner = fill ? c->d_path + 2 * c->path_cap + c->bpoff[g] : nullptr;
         d.path_cap = fill ? c->bfarness[g] : 0;
     }
     phase_begin(c, Ctx::kEvBfs);
@@ -291,7 +296,7 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
         c->bfarness[g] = c->h_prep_out[2 * B + g];
         c->bpoff[g + 1] = c->bpoff[g] + c->bfarness[g];
     }
-    if (cudaMalloc(&c->d_path, (size_t)std::max<int64_t>(1, c->bpoff[B]) * 4) != cudaSuccess)
+    if (cudaMalloc(&c->d_path, 3 * (size_t)std::max<int64_t>(1, c->bpoff[B]) * 4) != cudaSuccess)
         return fail(c, UST_ENOMEM, "BFS paths");
     c->path_cap = c->bpoff[B];
     rc = batch_prepare(c, true);

@@ -95,16 +95,23 @@ __global__ void __launch_bounds__(kScanThreads) path_offsets_kernel(int n, const
 }
 
 // path[ptr[v] .. ptr[v+1]) = bfs_parent(v), its parent, ..., u
+// Entry k of P(v): the edge (path[k], pchild[k]) = (a_j, a_{j-1}) with
+// a_0 = v, and its owner powner[k] = v.
 __global__ void path_fill_kernel(int n, int u, const int32_t *__restrict__ bpar, const int32_t *__restrict__ ptr,
-                                 int32_t *__restrict__ path)
+                                 int32_t *__restrict__ path, int32_t *__restrict__ pchild,
+                                 int32_t *__restrict__ powner)
 {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         int k = ptr[v];
         const int end = ptr[v + 1];
         int x = v;
         while (x != u && k < end) {
+            const int b = x;
             x = bpar[x];
-            path[k++] = x;
+            path[k] = x;
+            pchild[k] = b;
+            powner[k] = v;
+            ++k;
         }
     }
 }
@@ -151,12 +158,13 @@ int run_bfs(Ctx *c)
         cudaFree(c->d_path);
         c->d_path = nullptr;
         c->path_cap = 0;
-        if (cudaMalloc(&c->d_path, (size_t)c->farness * sizeof(int32_t)) != cudaSuccess)
+        if (cudaMalloc(&c->d_path, 3 * (size_t)c->farness * sizeof(int32_t)) != cudaSuccess)
             return fail(c, UST_ENOMEM, "BFS paths");
         c->path_cap = c->farness;
     }
     path_offsets_kernel<<<1, kScanThreads, 0, c->stream>>>(n, c->d_dist, c->d_pathptr);
-    path_fill_kernel<<<blocks, threads, 0, c->stream>>>(n, c->pivot, c->d_bpar, c->d_pathptr, c->d_path);
+    path_fill_kernel<<<blocks, threads, 0, c->stream>>>(n, c->pivot, c->d_bpar, c->d_pathptr, c->d_path,
+                                                        c->d_path + c->path_cap, c->d_path + 2 * c->path_cap);
     c->launches += 2;
     UST_CUDA_TRY(cudaGetLastError());
     return UST_OK;

@@ -36,6 +36,10 @@ struct GraphDesc {
     long long voff;            // offset of the graph's vertices in batch-wide arrays
     long long tree_begin;      // first tree id of the graph in this launch
     const int32_t *rp, *ci, *bpar, *path, *pathptr;
+    // entry p of the flattened BFS paths is the edge (path[p], pchild[p]) on
+    // P(powner[p]); fc = f^c(u) entries
+    const int32_t *pchild, *powner;
+    int fc;
 };
 
 // Graphs of at most this many vertices run the sampler with its per-tree
@@ -81,7 +85,7 @@ constexpr int kWsArrays = 13;
 struct PrepDesc {
     int n, u;
     const int32_t *rp, *ci;
-    int32_t *dist, *bpar, *pathptr, *path;
+    int32_t *dist, *bpar, *pathptr, *path, *pchild, *powner;
     long long path_cap;
 };
 // One graph of a batched diagonal combination.
@@ -107,7 +111,7 @@ struct Ctx {
     int32_t *d_rp = nullptr, *d_ci = nullptr;
     int32_t *d_bpar = nullptr, *d_dist = nullptr;
     int32_t *d_flag = nullptr;  // BFS level flag and misc small device scalars
-    int32_t *d_pathptr = nullptr, *d_path = nullptr;  // flattened BFS paths P(v)
+    int32_t *d_pathptr = nullptr, *d_path = nullptr;  // flattened BFS paths P(v): 3 x path_cap (ancestor, child, owner)
     int64_t path_cap = 0;
 
     // sampling

@@ -161,14 +161,21 @@ constexpr int kMarkMinWalk = 32;
 
 // Independent walks a thread keeps in flight in the walk passes.
 constexpr int kWalks = 4;
+// Algorithm-2 path entries a thread tests at once (shallow paths), and the
+// entries per vertex below which the flat form is used.
+constexpr int kPairs = 4;
 constexpr int kPathChunk = 4;
+constexpr int kFlatDepth = 8;
+// Sampler threads resident per SM that the register budget is sized for
+// (64 registers per thread at most).
+constexpr int kThreadsPerSm = 1024;
 
 // SM = true: the per-tree counters live in shared memory (n words, n < 2^16):
 // in-degrees as "total | remaining" 16-bit halves, then the popping rounds'
 // marks, then "pending children | size sum" 16-bit halves. SM = false: the
 // same counters in global memory, 32-bit halves of a 64-bit word.
 template <int BT, bool SM>
-__global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
+__global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kernel(SampleParams p)
 {
     extern __shared__ uint32_t s_dyn[];
     const int tid = threadIdx.x;
@@ -638,54 +645,113 @@ __global__ void __launch_bounds__(BT) sample_aggregate_kernel(SampleParams p)
         UST_PHASE(5);
 
         // ---- 3. Algorithm 2 ------------------------------------------------
-        // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u. Per chunk of edges the
-        // ancestors, their successors and the tested intervals are loaded
-        // independently of each other.
-        for (int v = tid; v < n; v += BT) {
-            if (v == u) continue;
-            const int pv = (int)(uint32_t)JA[v];
-            const int s0 = __ldg(gd.pathptr + v);
-            const int d = __ldg(gd.pathptr + v + 1) - s0;
-            int prevb = v, prevnb = nxt[v];
-            int cnt = 0;
-            for (int c = 0; c < d; c += kPathChunk) {
-                int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) {
-                    const int b = (j == 0) ? prevb : a[j - 1];
-                    const int nb = (j == 0) ? prevnb : na[j - 1];
-                    tx[j] = -1;
-                    sg[j] = 0;
-                    if (a[j] >= 0) {
-                        if (nb == a[j]) {
-                            tx[j] = b;
-                            sg[j] = 1;
-                        } else if (na[j] == b) {
-                            tx[j] = a[j];
-                            sg[j] = -1;
+        // Shallow BFS paths (f^c(u) <= kFlatDepth n): one independent test per
+        // path entry, updates of R by atomics. Deep paths: one thread per
+        // vertex walks its own path and adds its count once.
+        if (gd.fc <= kFlatDepth * n) {
+            // One independent test per entry q of the flattened paths: the edge
+            // (a, b) = (path[q], pchild[q]) of P(v), v = powner[q]. The tree
+            // uses it downwards (parent(b) = a: +1 when v lies in b's subtree) or
+            // upwards (parent(a) = b: -1 when v lies in a's subtree).
+            for (int q0 = tid; q0 - (tid & 31) < gd.fc; q0 += BT * kPairs) {  // uniform per warp
+                int a[kPairs], b[kPairs], v[kPairs];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    const int q = q0 + k * BT;
+                    const bool ok = q < gd.fc;
+                    a[k] = ok ? __ldg(gd.path + q) : -1;
+                    b[k] = ok ? __ldg(gd.pchild + q) : 0;
+                    v[k] = ok ? __ldg(gd.powner + q) : 0;
+                }
+                int na[kPairs], nb[kPairs], tx[kPairs], sg[kPairs];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    na[k] = (a[k] >= 0) ? nxt[a[k]] : -2;
+                    nb[k] = (a[k] >= 0) ? nxt[b[k]] : -2;
+                }
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    tx[k] = 0;
+                    sg[k] = 0;
+                    if (a[k] >= 0) {
+                        if (nb[k] == a[k]) {
+                            tx[k] = b[k];
+                            sg[k] = 1;
+                        } else if (na[k] == b[k]) {
+                            tx[k] = a[k];
+                            sg[k] = -1;
                         }
                     }
                 }
-                int lo[kPathChunk], sz[kPathChunk];
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) {
-                    lo[j] = (sg[j] != 0) ? (int)(uint32_t)JA[tx[j]] : 0;
-                    sz[j] = (sg[j] != 0) ? (SM ? (int)(C[tx[j]] & 0xFFFFu) : (int)(P[tx[j]] & 0xFFFFFFFFull)) + 1 : 0;
+                int lo[kPairs], sz[kPairs], pv[kPairs];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    lo[k] = (sg[k] != 0) ? (int)(uint32_t)JA[tx[k]] : 0;
+                    sz[k] = (sg[k] != 0) ? (SM ? (int)(C[tx[k]] & 0xFFFFu) : (int)(P[tx[k]] & 0xFFFFFFFFull)) + 1 : 0;
+                    pv[k] = (sg[k] != 0) ? (int)(uint32_t)JA[v[k]] : 0;
                 }
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j)
-                    if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
-                prevb = a[kPathChunk - 1];
-                prevnb = na[kPathChunk - 1];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    // lanes testing entries of the same vertex add up first, then
+                    // one of them updates R (consecutive entries share an owner)
+                    if (sg[k] != 0 && lo[k] <= pv[k] && pv[k] < lo[k] + sz[k]) {
+                        if (p.R_direct)
+                            atomicAdd(p.R_direct + gd.voff + v[k], (unsigned long long)(long long)sg[k]);
+                        else
+                            atomicAdd(Rp + v[k], sg[k]);
+                    }
+                }
             }
-            if (p.R_direct) {
-                if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
-            } else {
-                Rp[v] += cnt;
+        } else {
+            // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u. Per chunk of edges the
+            // ancestors, their successors and the tested intervals are loaded
+            // independently of each other.
+            for (int v = tid; v < n; v += BT) {
+                if (v == u) continue;
+                const int pv = (int)(uint32_t)JA[v];
+                const int s0 = __ldg(gd.pathptr + v);
+                const int d = __ldg(gd.pathptr + v + 1) - s0;
+                int prevb = v, prevnb = nxt[v];
+                int cnt = 0;
+                for (int c = 0; c < d; c += kPathChunk) {
+                    int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) {
+                        const int b = (j == 0) ? prevb : a[j - 1];
+                        const int nb = (j == 0) ? prevnb : na[j - 1];
+                        tx[j] = -1;
+                        sg[j] = 0;
+                        if (a[j] >= 0) {
+                            if (nb == a[j]) {
+                                tx[j] = b;
+                                sg[j] = 1;
+                            } else if (na[j] == b) {
+                                tx[j] = a[j];
+                                sg[j] = -1;
+                            }
+                        }
+                    }
+                    int lo[kPathChunk], sz[kPathChunk];
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) {
+                        lo[j] = (sg[j] != 0) ? (int)(uint32_t)JA[tx[j]] : 0;
+                        sz[j] = (sg[j] != 0) ? (SM ? (int)(C[tx[j]] & 0xFFFFu) : (int)(P[tx[j]] & 0xFFFFFFFFull)) + 1 : 0;
+                    }
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j)
+                        if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
+                    prevb = a[kPathChunk - 1];
+                    prevnb = na[kPathChunk - 1];
+                }
+                if (p.R_direct) {
+                    if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
+                } else {
+                    Rp[v] += cnt;
+                }
             }
         }
         __syncthreads();
@@ -734,7 +800,7 @@ __device__ __forceinline__ uint32_t half_add(uint32_t *words, int v, int delta)
 }
 
 template <int BT>
-__global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams p)
+__global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_kernel(SampleParams p)
 {
     extern __shared__ uint32_t s_dyn[];
     const int tid = threadIdx.x;
@@ -1187,59 +1253,116 @@ __global__ void __launch_bounds__(BT) sample_aggregate_smem_kernel(SampleParams 
         UST_PHASE(8);
 
         // ---- 3. Algorithm 2 ------------------------------------------------
-        // C[x] = parent(x) << 16 | pre(x); parent(u) reads as 0xFFFF.
-        for (int v = tid; v < n; v += BT) {
-            if (v == u) continue;
-            const uint32_t cv = C[v];
-            const int pv = (int)(cv & 0xFFFFu);
-            const int s0 = __ldg(gd.pathptr + v);
-            const int d = __ldg(gd.pathptr + v + 1) - s0;
-            int prevb = v, prevnb = (int)(cv >> 16), prevpre = pv;
-            int cnt = 0;
-            for (int c = 0; c < d; c += kPathChunk) {
-                int a[kPathChunk], na[kPathChunk], pa[kPathChunk], tx[kPathChunk], sg[kPathChunk], lo[kPathChunk];
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) {
-                    const uint32_t w = (a[j] >= 0) ? C[a[j]] : 0xFFFE0000u;
-                    na[j] = (int)(w >> 16);
-                    pa[j] = (int)(w & 0xFFFFu);
+        // Shallow BFS paths (f^c(u) <= kFlatDepth n): one independent test per
+        // path entry, updates of R by atomics. Deep paths: one thread per
+        // vertex walks its own path and adds its count once.
+        if (gd.fc <= kFlatDepth * n) {
+            // One independent test per entry q of the flattened paths: the edge
+            // (a, b) = (path[q], pchild[q]) of P(v), v = powner[q]; downwards
+            // (parent(b) = a) it adds +1 when v lies in b's subtree, upwards
+            // (parent(a) = b) -1 when v lies in a's subtree.
+            // C[x] = parent(x) << 16 | pre(x); parent(u) reads as 0xFFFF.
+            for (int q0 = tid; q0 - (tid & 31) < gd.fc; q0 += BT * kPairs) {  // uniform per warp
+                int a[kPairs], b[kPairs], v[kPairs];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    const int q = q0 + k * BT;
+                    const bool ok = q < gd.fc;
+                    a[k] = ok ? __ldg(gd.path + q) : -1;
+                    b[k] = ok ? __ldg(gd.pchild + q) : 0;
+                    v[k] = ok ? __ldg(gd.powner + q) : 0;
                 }
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) {
-                    const int b = (j == 0) ? prevb : a[j - 1];
-                    const int nb = (j == 0) ? prevnb : na[j - 1];
-                    const int pb = (j == 0) ? prevpre : pa[j - 1];
-                    tx[j] = -1;
-                    sg[j] = 0;
-                    lo[j] = 0;
-                    if (a[j] >= 0) {
-                        if (nb == a[j]) {  // the tree uses (a, b) downwards: interval of b
-                            tx[j] = b;
-                            sg[j] = 1;
-                            lo[j] = pb;
-                        } else if (na[j] == b) {  // upwards: interval of a
-                            tx[j] = a[j];
-                            sg[j] = -1;
-                            lo[j] = pa[j];
+                int tx[kPairs], sg[kPairs], lo[kPairs], pv[kPairs];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    tx[k] = 0;
+                    sg[k] = 0;
+                    lo[k] = 0;
+                    pv[k] = 0;
+                    if (a[k] >= 0) {
+                        const uint32_t ca = C[a[k]], cb = C[b[k]];
+                        pv[k] = (int)(C[v[k]] & 0xFFFFu);
+                        if ((int)(cb >> 16) == a[k]) {  // the tree uses (a, b) downwards: interval of b
+                            tx[k] = b[k];
+                            sg[k] = 1;
+                            lo[k] = (int)(cb & 0xFFFFu);
+                        } else if ((int)(ca >> 16) == b[k]) {  // upwards: interval of a
+                            tx[k] = a[k];
+                            sg[k] = -1;
+                            lo[k] = (int)(ca & 0xFFFFu);
                         }
                     }
                 }
-                int sz[kPathChunk];
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j) sz[j] = (sg[j] != 0) ? gsz[tx[j]] : 0;
-#pragma unroll
-                for (int j = 0; j < kPathChunk; ++j)
-                    if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
-                prevb = a[kPathChunk - 1];
-                prevnb = na[kPathChunk - 1];
-                prevpre = pa[kPathChunk - 1];
+                int sz[kPairs];
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) sz[k] = (sg[k] != 0) ? gsz[tx[k]] : 0;
+    #pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    // lanes testing entries of the same vertex add up first, then
+                    // one of them updates R (consecutive entries share an owner)
+                    if (sg[k] != 0 && lo[k] <= pv[k] && pv[k] < lo[k] + sz[k]) {
+                        if (p.R_direct)
+                            atomicAdd(p.R_direct + gd.voff + v[k], (unsigned long long)(long long)sg[k]);
+                        else
+                            atomicAdd(Rp + v[k], sg[k]);
+                    }
+                }
             }
-            if (p.R_direct) {
-                if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
-            } else {
-                Rp[v] += cnt;
+        } else {
+            // C[x] = parent(x) << 16 | pre(x); parent(u) reads as 0xFFFF.
+            for (int v = tid; v < n; v += BT) {
+                if (v == u) continue;
+                const uint32_t cv = C[v];
+                const int pv = (int)(cv & 0xFFFFu);
+                const int s0 = __ldg(gd.pathptr + v);
+                const int d = __ldg(gd.pathptr + v + 1) - s0;
+                int prevb = v, prevnb = (int)(cv >> 16), prevpre = pv;
+                int cnt = 0;
+                for (int c = 0; c < d; c += kPathChunk) {
+                    int a[kPathChunk], na[kPathChunk], pa[kPathChunk], tx[kPathChunk], sg[kPathChunk], lo[kPathChunk];
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) {
+                        const uint32_t w = (a[j] >= 0) ? C[a[j]] : 0xFFFE0000u;
+                        na[j] = (int)(w >> 16);
+                        pa[j] = (int)(w & 0xFFFFu);
+                    }
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) {
+                        const int b = (j == 0) ? prevb : a[j - 1];
+                        const int nb = (j == 0) ? prevnb : na[j - 1];
+                        const int pb = (j == 0) ? prevpre : pa[j - 1];
+                        tx[j] = -1;
+                        sg[j] = 0;
+                        lo[j] = 0;
+                        if (a[j] >= 0) {
+                            if (nb == a[j]) {  // the tree uses (a, b) downwards: interval of b
+                                tx[j] = b;
+                                sg[j] = 1;
+                                lo[j] = pb;
+                            } else if (na[j] == b) {  // upwards: interval of a
+                                tx[j] = a[j];
+                                sg[j] = -1;
+                                lo[j] = pa[j];
+                            }
+                        }
+                    }
+                    int sz[kPathChunk];
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j) sz[j] = (sg[j] != 0) ? gsz[tx[j]] : 0;
+    #pragma unroll
+                    for (int j = 0; j < kPathChunk; ++j)
+                        if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
+                    prevb = a[kPathChunk - 1];
+                    prevnb = na[kPathChunk - 1];
+                    prevpre = pa[kPathChunk - 1];
+                }
+                if (p.R_direct) {
+                    if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
+                } else {
+                    Rp[v] += cnt;
+                }
             }
         }
         __syncthreads();
@@ -1445,9 +1568,13 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     gd.bpar = c->d_bpar;
     gd.path = c->d_path;
     gd.pathptr = c->d_pathptr;
+    gd.pchild = c->d_path + c->path_cap;
+    gd.powner = c->d_path + 2 * c->path_cap;
+    gd.fc = (int)c->farness;
     const GraphDesc &o = c->single_desc;
     const bool same = o.n == gd.n && o.u == gd.u && o.graph == gd.graph && o.rp == gd.rp && o.ci == gd.ci &&
-                      o.bpar == gd.bpar && o.path == gd.path && o.pathptr == gd.pathptr;
+                      o.bpar == gd.bpar && o.path == gd.path && o.pathptr == gd.pathptr && o.pchild == gd.pchild &&
+                      o.powner == gd.powner && o.fc == gd.fc;
     if (!c->single_desc_valid || !same) {
         c->single_desc = gd;
         const long long starts[2] = {0, kOpenEnd};
@@ -1530,7 +1657,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
 // size; the caller passes only its inputs and its output.
 //
 // Limits: n <= kNoAllocMaxN vertices and f^c(u) = sum_v dist(u, v) <=
-// kNoAllocMaxPath. The array is about 8.5 MB and stays resident on every GPU
+// kNoAllocMaxPath. The array is about 10.6 MB and stays resident on every GPU
 // that loads this library until the process exits. Every call reuses it and
 // overwrites the previous contents, so calls that overlap on the GPU (two
 // streams, two host threads) race and must be serialised by the caller.
@@ -1551,7 +1678,7 @@ constexpr long long kNaDist = kNaRp + (long long)kNoAllocCtas * kNoAllocMaxN;
 constexpr long long kNaBpar = kNaDist + kNoAllocMaxN;
 constexpr long long kNaPathPtr = kNaBpar + kNoAllocMaxN;
 constexpr long long kNaPath = kNaPathPtr + ((kNoAllocMaxN + 1 + 31) / 32) * 32;
-constexpr long long kNaStats = kNaPath + kNoAllocMaxPath;
+constexpr long long kNaStats = kNaPath + 3ll * kNoAllocMaxPath;  // ancestors, children, owners
 constexpr long long kNaDesc = kNaStats + 2 * 32;  // one GraphDesc and two item starts
 constexpr long long kNaWords = kNaDesc + 64;
 static_assert(sizeof(GraphDesc) + 2 * sizeof(long long) <= 64 * sizeof(int32_t), "descriptor slot");
@@ -1565,8 +1692,9 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[kNaWords];
 // many path entries).
 constexpr int kPrepThreads = 1024;
 __device__ void prepare_graph(int n, int u, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                              int32_t *dist, int32_t *bpar, int32_t *pathptr, int32_t *path, long long path_cap,
-                              int *status, int *ecc_out = nullptr, int *fc_out = nullptr)
+                              int32_t *dist, int32_t *bpar, int32_t *pathptr, int32_t *path, int32_t *pchild,
+                              int32_t *powner, long long path_cap, int *status, int *ecc_out = nullptr,
+                              int *fc_out = nullptr)
 {
     __shared__ int s_warp[kPrepThreads / 32 + 1];
     __shared__ int s_bad;
@@ -1640,8 +1768,12 @@ __device__ void prepare_graph(int n, int u, const int32_t *__restrict__ rp, cons
         const int end = pathptr[v + 1];
         int x = v;
         while (x != u && k < end) {
+            const int b = x;
             x = bpar[x];
-            path[k++] = x;
+            path[k] = x;
+            pchild[k] = b;
+            powner[k] = v;
+            ++k;
         }
     }
 }
@@ -1650,6 +1782,7 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
                                                                        const int32_t *__restrict__ rp,
                                                                        const int32_t *__restrict__ ci, int32_t *dist,
                                                                        int32_t *bpar, int32_t *pathptr, int32_t *path,
+                                                                       int32_t *pchild, int32_t *powner,
                                                                        int path_cap, int *status, GraphDesc *desc,
                                                                        long long *item_start)
 {
@@ -1665,11 +1798,14 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
         d.bpar = bpar;
         d.path = path;
         d.pathptr = pathptr;
+        d.pchild = pchild;
+        d.powner = powner;
+        d.fc = 0;  // set below, once f^c(u) is known
         *desc = d;
         item_start[0] = 0;
         item_start[1] = kOpenEnd;
     }
-    prepare_graph(n, u, rp, ci, dist, bpar, pathptr, path, path_cap, status);
+    prepare_graph(n, u, rp, ci, dist, bpar, pathptr, path, pchild, powner, path_cap, status, nullptr, &desc->fc);
 }
 
 // Device address of g_noalloc_scratch, looked up once per device.
@@ -1714,7 +1850,9 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
     GraphDesc *desc = reinterpret_cast<GraphDesc *>(base + kNaDesc);
     long long *item_start = reinterpret_cast<long long *>(desc + 1);
     noalloc_prepare_kernel<<<1, kPrepThreads, 0, st>>>(n, pivot, (uint32_t)graph_id, row_ptr, col_idx, dist, bpar,
-                                                        pathptr, path, kNoAllocMaxPath, status, desc, item_start);
+                                                        pathptr, path, path + kNoAllocMaxPath,
+                                                        path + 2 * kNoAllocMaxPath, kNoAllocMaxPath, status, desc,
+                                                        item_start);
     if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
     unsigned long long h_stats[32];
     if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess) return UST_ECUDA;
@@ -1770,8 +1908,8 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prepare_kernel(const PrepD
                                                                      int *out)
 {
     const PrepDesc g = d[blockIdx.x];
-    prepare_graph(g.n, g.u, g.rp, g.ci, g.dist, g.bpar, g.pathptr, g.path, g.path_cap, out + blockIdx.x,
-                  out + count + blockIdx.x, out + 2 * count + blockIdx.x);
+    prepare_graph(g.n, g.u, g.rp, g.ci, g.dist, g.bpar, g.pathptr, g.path, g.pchild, g.powner, g.path_cap,
+                  out + blockIdx.x, out + count + blockIdx.x, out + 2 * count + blockIdx.x);
 }
 
 // diag of graph blockIdx.x: L^+[u,u] = x_u, L^+[v,v] = (R[v]/tau - x_u) + 2 x_v
