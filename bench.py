@@ -36,7 +36,7 @@ SEED = 0
 # DRAM bytes (read + write) of one sampler launch on the rmat16 workload, from the ncu capture
 # summarised in profiles/sample_aggregate_rmat16.md. Reported only while the kernel source is
 # the one the capture was taken on.
-TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "f477f1df45caf052fcb03224094f8af600da153d", "bytes": 1.680338e9 + 3.968391e9}
+TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "c2173353de3126561f5c28f6e9f014d1a09a8702", "bytes": 1.999768e9 + 4.072733e9}
 
 # workload -> (description, oracle sample in trees for the CPU baseline; None = all)
 WORKLOADS = {
