@@ -70,25 +70,6 @@ namespace ust {
 // Host checks of the CSR contract: row_ptr monotone from 0 to nnz, columns
 // in range and strictly increasing per row, no self-loops, every arc present
 // in both directions, no isolated vertex.
-int validate_csr(Ctx *c, int n, int nnz, const int32_t *rp, const int32_t *ci)
-{
-    if (rp[0] != 0 || rp[n] != nnz) return ust::fail(c, UST_EINVAL, "row_ptr must run from 0 to nnz");
-    for (int v = 0; v < n; ++v) {
-        const int b = rp[v], e = rp[v + 1];
-        if (e < b) return ust::fail(c, UST_EINVAL, "row_ptr is not monotone");
-        if (e == b) return ust::fail(c, UST_ENOTCONNECTED, "isolated vertex");
-        for (int k = b; k < e; ++k) {
-            const int w = ci[k];
-            if (w < 0 || w >= n) return ust::fail(c, UST_EINVAL, "column index out of range");
-            if (w == v) return ust::fail(c, UST_EINVAL, "self-loop");
-            if (k > b && ci[k - 1] >= w) return ust::fail(c, UST_EINVAL, "row not strictly increasing");
-            if (!std::binary_search(ci + rp[w], ci + rp[w + 1], v))
-                return ust::fail(c, UST_EINVAL, "CSR is not symmetric");
-        }
-    }
-    return UST_OK;
-}
-
 int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, const ust_opts &op);
 int batch_sample_aggregate(Ctx *c, int64_t n_trees, uint64_t seed);
 int64_t batch_tau(const Ctx *c, double eps);
@@ -99,8 +80,6 @@ int batch_reset(Ctx *c);
 }  // namespace ust
 
 namespace {
-
-using ust::validate_csr;
 
 // Context options shared by single graphs and batches.
 int apply_opts(Ctx *c, const ust_opts &op, int n)
@@ -131,21 +110,6 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     const int orc = apply_opts(c, op, n);
     if (orc) return orc;
 
-    if (!op.skip_validation) {
-        std::vector<int32_t> hrp, hci;
-        const int32_t *rp = g->row_ptr, *ci = g->col_idx;
-        if (g->on_device) {
-            hrp.resize((size_t)n + 1);
-            hci.resize((size_t)nnz);
-            UST_CUDA_TRY(cudaMemcpy(hrp.data(), g->row_ptr, hrp.size() * 4, cudaMemcpyDeviceToHost));
-            UST_CUDA_TRY(cudaMemcpy(hci.data(), g->col_idx, hci.size() * 4, cudaMemcpyDeviceToHost));
-            rp = hrp.data();
-            ci = hci.data();
-        }
-        const int rc = validate_csr(c, n, nnz, rp, ci);
-        if (rc) return rc;
-    }
-
     if (cudaMalloc(&c->d_rp, ((size_t)n + 1) * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "row_ptr");
     if (cudaMalloc(&c->d_ci, (size_t)nnz * 4) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "col_idx");
     const cudaMemcpyKind kind = g->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -164,6 +128,12 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     if (cudaMalloc(&c->d_Rtmp, (size_t)n * 8) != cudaSuccess) return ust::fail(c, UST_ENOMEM, "counts");
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)n * 8, c->stream));
 
+    // the input checks run on the device copy (the BFS then finds any vertex
+    // that is not connected to the pivot)
+    if (!op.skip_validation) {
+        const int rc = ust::check_graph(c, n, nnz, c->d_rp, c->d_ci, c->d_flag);
+        if (rc) return rc;
+    }
     int rc = ust::run_bfs(c);
     if (rc) return rc;
     rc = ust::alloc_sampler(c, op.block_threads, op.ctas_per_sm);

@@ -18,7 +18,6 @@
 
 namespace ust {
 
-int validate_csr(Ctx *c, int n, int nnz, const int32_t *rp, const int32_t *ci);
 
 namespace {
 
@@ -233,30 +232,16 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
     }
 
     // host copies of the row pointers (validation, heavy rows)
+    // host copies of the row pointers (heavy rows, the path space); the
+    // input checks run on the device copies below
     std::vector<int32_t> hrp((size_t)c->n + B);
-    {
-        std::vector<int32_t> hci;
-        for (int g = 0; g < B; ++g) {
-            int32_t *dst = hrp.data() + c->bvoff[g] + g;
-            const size_t rb = ((size_t)gs[g].n + 1) * 4;
-            if (gs[g].on_device)
-                UST_CUDA_TRY(cudaMemcpy(dst, gs[g].row_ptr, rb, cudaMemcpyDeviceToHost));
-            else
-                memcpy(dst, gs[g].row_ptr, rb);
-            if (!op.skip_validation) {
-                const int32_t *ci = gs[g].col_idx;
-                if (gs[g].on_device) {
-                    hci.resize((size_t)gs[g].nnz);
-                    UST_CUDA_TRY(cudaMemcpy(hci.data(), gs[g].col_idx, hci.size() * 4, cudaMemcpyDeviceToHost));
-                    ci = hci.data();
-                }
-                const int rc = validate_csr(c, gs[g].n, gs[g].nnz, dst, ci);
-                if (rc) {
-                    c->err = "graph " + std::to_string(g) + ": " + c->err;
-                    return rc;
-                }
-            }
-        }
+    for (int g = 0; g < B; ++g) {
+        int32_t *dst = hrp.data() + c->bvoff[g] + g;
+        const size_t rb = ((size_t)gs[g].n + 1) * 4;
+        if (gs[g].on_device)
+            UST_CUDA_TRY(cudaMemcpy(dst, gs[g].row_ptr, rb, cudaMemcpyDeviceToHost));
+        else
+            memcpy(dst, gs[g].row_ptr, rb);
     }
     const size_t nv = (size_t)c->n, na = (size_t)c->nnz;
     if (cudaMalloc(&c->d_rp, (nv + B) * 4) != cudaSuccess) return fail(c, UST_ENOMEM, "row_ptr");
@@ -279,6 +264,16 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
         UST_CUDA_TRY(cudaMemcpyAsync(c->d_ci + c->baoff[g], gs[g].col_idx, (size_t)gs[g].nnz * 4, kind, c->stream));
     }
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, nv * 8, c->stream));
+    if (!op.skip_validation) {
+        for (int g = 0; g < B; ++g) {
+            const int rc = check_graph(c, c->bn[g], c->bnnz[g], c->d_rp + c->bvoff[g] + g, c->d_ci + c->baoff[g],
+                                       c->d_flag);
+            if (rc) {
+                c->err = "graph " + std::to_string(g) + ": " + c->err;
+                return rc;
+            }
+        }
+    }
 
     // B_u of every graph: a first pass measures f^c(u) (no path space yet),
     // the second fills the paths

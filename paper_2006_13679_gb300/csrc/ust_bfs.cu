@@ -4,6 +4,8 @@
 // vertex scans its sorted adjacency row and stops at the first neighbour at
 // distance L. Because rows are sorted, that neighbour is the smallest-id
 // vertex one level closer to u, which is the parent rule of B_u.
+#include <algorithm>
+
 #include "ust_common.cuh"
 
 namespace ust {
@@ -116,7 +118,85 @@ __global__ void path_fill_kernel(int n, int u, const int32_t *__restrict__ bpar,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Input checks of ust_init on the device copy of the CSR (the same checks
+// the host would make, at GPU speed). Errors are OR-ed into *bad.
+enum : int {
+    kBadBounds = 1,    // row_ptr does not run from 0 to nnz, or is not monotone
+    kBadRange = 2,     // a column index outside [0, n)
+    kBadLoop = 4,      // a self-loop
+    kBadOrder = 8,     // a row not strictly increasing (unsorted or duplicate)
+    kBadSymmetry = 16, // an arc (v, w) without (w, v)
+    kIsolated = 32,    // a vertex without arcs
+};
+
+__global__ void check_rows_kernel(int n, int nnz, const int32_t *__restrict__ rp, int *bad)
+{
+    int flags = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) flags |= kBadBounds;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int b = __ldg(rp + v), e = __ldg(rp + v + 1);
+        if (e < b || b < 0 || e > nnz) flags |= kBadBounds;
+        else if (e == b) flags |= kIsolated;
+    }
+    if (flags) atomicOr(bad, flags);
+}
+
+// Needs monotone row pointers from 0 to nnz (check_rows_kernel first).
+__global__ void check_arcs_kernel(int n, int nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                  int *bad)
+{
+    int flags = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;  // the row of arc k: the largest v with rp[v] <= k
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(rp + mid) <= k) lo = mid; else hi = mid;
+        }
+        const int v = lo, w = __ldg(ci + k);
+        if (w < 0 || w >= n) {
+            flags |= kBadRange;
+            continue;
+        }
+        if (w == v) flags |= kBadLoop;
+        if (k > __ldg(rp + v) && __ldg(ci + k - 1) >= w) flags |= kBadOrder;
+        int a = __ldg(rp + w), z = __ldg(rp + w + 1);  // v in row w (sorted when the graph is valid)
+        while (a < z) {
+            const int mid = (a + z) >> 1;
+            if (__ldg(ci + mid) < v) a = mid + 1; else z = mid;
+        }
+        if (a >= __ldg(rp + w + 1) || __ldg(ci + a) != v) flags |= kBadSymmetry;
+    }
+    if (flags) atomicOr(bad, flags);
+}
+
 }  // namespace
+
+int check_graph(Ctx *c, int n, int nnz, const int32_t *d_rp, const int32_t *d_ci, int *d_bad)
+{
+    const int threads = 256;
+    const int rows = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    const int arcs = (int)std::min<int64_t>(((int64_t)nnz + threads - 1) / threads, (int64_t)c->num_sms * 16);
+    int bad = 0;
+    UST_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    check_rows_kernel<<<std::max(1, rows), threads, 0, c->stream>>>(n, nnz, d_rp, d_bad);
+    c->launches += 1;
+    UST_CUDA_TRY(cudaGetLastError());
+    UST_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (bad & kBadBounds) return fail(c, UST_EINVAL, "row_ptr must run from 0 to nnz and be monotone");
+    check_arcs_kernel<<<std::max(1, arcs), threads, 0, c->stream>>>(n, nnz, d_rp, d_ci, d_bad);
+    c->launches += 1;
+    UST_CUDA_TRY(cudaGetLastError());
+    UST_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (bad & kBadRange) return fail(c, UST_EINVAL, "column index out of range");
+    if (bad & kBadLoop) return fail(c, UST_EINVAL, "self-loop");
+    if (bad & kBadOrder) return fail(c, UST_EINVAL, "row not strictly increasing");
+    if (bad & kBadSymmetry) return fail(c, UST_EINVAL, "CSR is not symmetric");
+    if (bad & kIsolated) return fail(c, UST_ENOTCONNECTED, "isolated vertex");
+    return UST_OK;
+}
 
 int run_bfs(Ctx *c)
 {

@@ -210,6 +210,8 @@ inline void phase_close(Ctx *c, int ph)
 
 // Host drivers (one per translation unit).
 int run_bfs(Ctx *c);
+// The input checks of ust_init on a device CSR; d_bad: one int of scratch.
+int check_graph(Ctx *c, int n, int nnz, const int32_t *d_rp, const int32_t *d_ci, int *d_bad);
 // Chooses the single-graph launch shape (requested or automatic) and sizes
 // the workspace for it.
 int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm);

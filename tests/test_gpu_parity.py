@@ -295,3 +295,33 @@ def test_sharded_tree_ranges_equal_one_run(pkg, orc):
         np.testing.assert_array_equal(h2.diag(), h1.diag())
         with pytest.raises(pkg.UstError):
             h2.set_counts(R, 0)
+
+
+@pytest.mark.parametrize("case,rp,ci,code", [
+    ("row_ptr not monotone", [0, 2, 1, 4], [1, 2, 0, 0], "EINVAL"),
+    ("row_ptr end != nnz", [0, 1, 2, 2], [1, 0, 0], "EINVAL"),
+    ("column out of range", [0, 1, 2], [1, 2], "EINVAL"),
+    ("self-loop", [0, 2, 3], [0, 1, 0], "EINVAL"),
+    ("unsorted row", [0, 2, 3, 4], [2, 1, 0, 0], "EINVAL"),
+    ("duplicate arc", [0, 2, 4], [1, 1, 0, 0], "EINVAL"),
+    ("asymmetric", [0, 2, 4, 5], [1, 2, 0, 2, 0], "EINVAL"),
+    ("isolated vertex", [0, 1, 2, 2], [1, 0], "ENOTCONNECTED"),
+])
+def test_input_checks_on_device(pkg, case, rp, ci, code):
+    """ust_init checks the CSR on the device: every malformed input is
+    rejected with its error code and nothing else runs on it."""
+    rp = np.array(rp, dtype=np.int32)
+    ci = np.array(ci, dtype=np.int32)
+    with pytest.raises(pkg.UstError) as e:
+        pkg.UST(rp, ci, 0)
+    assert e.value.code == getattr(pkg, "UST_" + code), case
+
+
+def test_batch_input_checks_name_the_graph(pkg):
+    good = synth.grid(4, 4)
+    bad_rp = np.array([0, 2, 4, 5], dtype=np.int32)
+    bad_ci = np.array([1, 2, 0, 2, 0], dtype=np.int32)  # 1 -> 2 without 2 -> 1
+    with pytest.raises(pkg.UstError) as e:
+        pkg.USTBatch([(good.row_ptr, good.col_idx), (bad_rp, bad_ci)], [0, 0])
+    assert e.value.code == pkg.UST_EINVAL
+    assert "graph 1" in str(e.value)
