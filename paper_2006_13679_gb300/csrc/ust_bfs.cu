@@ -198,8 +198,49 @@ int check_graph(Ctx *c, int n, int nnz, const int32_t *d_rp, const int32_t *d_ci
     return UST_OK;
 }
 
+// Small graphs: one CTA does the BFS, the prefix and the paths in one
+// launch; a second launch only when the path space has to grow.
+int run_bfs_small(Ctx *c)
+{
+    int32_t *h_out = reinterpret_cast<int32_t *>(c->h_stats);
+    phase_begin(c, Ctx::kEvBfs);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        PrepDesc d;
+        d.n = c->n;
+        d.u = c->pivot;
+        d.rp = c->d_rp;
+        d.ci = c->d_ci;
+        d.dist = c->d_dist;
+        d.bpar = c->d_bpar;
+        d.pathptr = c->d_pathptr;
+        d.path = c->d_path;
+        d.pchild = c->d_path ? c->d_path + c->path_cap : nullptr;
+        d.powner = c->d_path ? c->d_path + 2 * c->path_cap : nullptr;
+        d.path_cap = c->d_path ? c->path_cap : 0;
+        UST_CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, 3 * sizeof(int32_t), c->stream));
+        const int rc = run_prepare_single(c, d, c->d_flag);
+        if (rc) return rc;
+        UST_CUDA_TRY(cudaMemcpyAsync(h_out, c->d_flag, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (h_out[0] & 1) return fail(c, UST_ENOTCONNECTED, "graph is not connected");
+        c->ecc = h_out[1];
+        c->farness = h_out[2];
+        if (!(h_out[0] & 2)) break;  // the paths are in place
+        if (attempt == 1) return fail(c, UST_ECUDA, "B_u: path space mismatch");
+        cudaFree(c->d_path);
+        c->d_path = nullptr;
+        c->path_cap = 0;
+        if (cudaMalloc(&c->d_path, 3 * (size_t)c->farness * sizeof(int32_t)) != cudaSuccess)
+            return fail(c, UST_ENOMEM, "BFS paths");
+        c->path_cap = c->farness;
+    }
+    phase_end(c, Ctx::kEvBfs);
+    return UST_OK;
+}
+
 int run_bfs(Ctx *c)
 {
+    if (c->n <= kPrepMaxN) return run_bfs_small(c);
     const int n = c->n;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);

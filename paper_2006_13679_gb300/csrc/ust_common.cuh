@@ -222,6 +222,12 @@ int alloc_batch_sampler(Ctx *c, int block_threads, int ctas_per_sm);
 int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
                 int32_t *d_pops_out, int64_t *draws, int64_t *rounds, int *max_rounds, int *max_depth);
 int run_batch_prepare(Ctx *c, const PrepDesc *d_desc, int count, int *d_out);
+// B_u, ecc, f^c(u) and (when they fit path_cap) the paths of one graph in one
+// CTA; d_out: status, ecc, f^c(u).
+int run_prepare_single(Ctx *c, const PrepDesc &d, int *d_out);
+// Single graphs up to this many vertices get B_u from one CTA in one launch
+// (f^c(u) < n^2 / 2 stays below 2^31).
+constexpr int kPrepMaxN = 32768;
 int run_batch_combine(Ctx *c, const CombineDesc *d_desc, int count, double *d_diag);
 int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, const long long *d_item_start,
                       int ngraphs, long long total_items, int max_n, long long max_rounds, uint64_t seed,

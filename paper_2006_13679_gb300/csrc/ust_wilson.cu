@@ -1912,6 +1912,13 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prepare_kernel(const PrepD
                   out + blockIdx.x, out + count + blockIdx.x, out + 2 * count + blockIdx.x);
 }
 
+// B_u of one graph in one CTA (small single graphs): out as above, count 1.
+__global__ void __launch_bounds__(kPrepThreads) single_prepare_kernel(PrepDesc g, int *out)
+{
+    prepare_graph(g.n, g.u, g.rp, g.ci, g.dist, g.bpar, g.pathptr, g.path, g.pchild, g.powner, g.path_cap, out,
+                  out + 1, out + 2);
+}
+
 // diag of graph blockIdx.x: L^+[u,u] = x_u, L^+[v,v] = (R[v]/tau - x_u) + 2 x_v
 __global__ void batch_combine_kernel(const CombineDesc *__restrict__ d, const long long *__restrict__ R,
                                      const double *__restrict__ x, double *__restrict__ diag)
@@ -1932,6 +1939,14 @@ __global__ void batch_combine_kernel(const CombineDesc *__restrict__ d, const lo
 }
 
 }  // namespace
+
+int run_prepare_single(Ctx *c, const PrepDesc &d, int *d_out)
+{
+    single_prepare_kernel<<<1, kPrepThreads, 0, c->stream>>>(d, d_out);
+    c->launches += 1;
+    UST_CUDA_TRY(cudaGetLastError());
+    return UST_OK;
+}
 
 int run_batch_prepare(Ctx *c, const PrepDesc *d_desc, int count, int *d_out)
 {
