@@ -189,6 +189,18 @@ UST_API int ust_sample_aggregate(ust_ctx *c, int64_t n_trees, uint64_t seed);
  * trees and eps <= 0), UST_ENOTCONVERGED, UST_ETIMEOUT, UST_ECUDA. */
 UST_API int ust_diag(ust_ctx *c, double eps, double *diag_out, int32_t out_on_device);
 
+/* Centralities that depend only on diag(L^+) (Section 3.1, Eq. elec-farness;
+ * the normalized random-walk betweenness lemma; the Kirchhoff index
+ * K = n tr(L^+)), from the estimate of ust_diag(c, eps, ...):
+ *   closeness_out[v] = (n - 1) / (n L+[v,v] + tr(L+))    electrical closeness
+ *   nrwb_out[v]      = 1/n + tr(L+) / ((n - 1) (n L+[v,v] + tr(L+)))
+ *   kirchhoff_out[g] = n tr(L+)                           one per graph
+ * n doubles each (a batch: its total n, laid out as the diagonals; one
+ * Kirchhoff index per graph); any output may be NULL. The trace is a
+ * fixed-order FP64 sum. Errors as ust_diag. */
+UST_API int ust_centralities(ust_ctx *c, double eps, double *closeness_out, double *nrwb_out, double *kirchhoff_out,
+                             int32_t out_on_device);
+
 /* Sample size tau(eps) of Algorithm 1 for this graph and pivot. */
 UST_API int64_t ust_tau(const ust_ctx *c, double eps);
 

@@ -14,7 +14,8 @@ Two layers:
 * numpy/scipy helpers in this file: the dense closed form
   L^+ = (L + J/n)^{-1} - J/n (Section 2.1), effective resistances from it
   (Eq. eff-res), brute-force spanning-tree enumeration and the matrix-tree
-  count, which pin the C layer in the tests.
+  count, which pin the C layer in the tests; and the centralities that
+  depend only on the diagonal (closeness, NRWB, Kirchhoff index).
 """
 from __future__ import annotations
 
@@ -194,6 +195,23 @@ def combine(R: np.ndarray, tau: int, x: np.ndarray, u: int) -> np.ndarray:
     d = np.zeros(n, dtype=np.float64)
     lib().orc_combine(n, _p(Rc, ctypes.c_int64), tau, _p(xc, ctypes.c_double), u, _p(d, ctypes.c_double))
     return d
+
+
+def centralities(diag) -> dict:
+    """Centralities from a diagonal of L^+, written out from the paper:
+    electrical farness f(v) = n L+[v,v] + tr(L+) (Section 3.1, Eq.
+    elec-farness), electrical closeness (n - 1) / f(v) (Section 2,
+    electrical closeness), normalized random-walk betweenness
+    1/n + tr(L+) / ((n - 1) f(v)) (the NRWB lemma of Section 3.3, derived in
+    the appendix) and the Kirchhoff index n tr(L+) (appendix on the Kirchhoff
+    index). The NRWB form is the lemma's: the definition as printed sums
+    per-target ratios, the derivation takes the ratio of the summed
+    numerators and denominators, and the method computes the latter."""
+    d = np.asarray(diag, dtype=np.float64)
+    n = d.shape[0]
+    tr = float(d.sum())
+    f = n * d + tr
+    return {"farness": f, "closeness": (n - 1) / f, "nrwb": 1.0 / n + tr / ((n - 1) * f), "kirchhoff": n * tr}
 
 
 def tau(ecc: int, m: int, eps: float, delta: float, kappa: float = 0.3) -> int:

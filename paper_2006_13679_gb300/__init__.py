@@ -130,6 +130,17 @@ class UST:
         check(load().ust_diag(self._h, float(eps), p, dev), self._h)
         return out
 
+    def centralities(self, eps: float = 0.0) -> dict:
+        """Electrical closeness, normalized random-walk betweenness (n each)
+        and Kirchhoff index (one per graph) from the diagonal estimate."""
+        count = getattr(self, "count", 1)
+        cl = np.empty(self.n, dtype=np.float64)
+        nr = np.empty(self.n, dtype=np.float64)
+        kf = np.empty(count, dtype=np.float64)
+        check(load().ust_centralities(self._h, float(eps), ctypes.c_void_p(cl.ctypes.data),
+                                      ctypes.c_void_p(nr.ctypes.data), ctypes.c_void_p(kf.ctypes.data), 0), self._h)
+        return {"closeness": cl, "nrwb": nr, "kirchhoff": kf if count > 1 else float(kf[0])}
+
     def counts(self, out=None):
         out, p, dev = self._out(out, np.int64, self.n)
         check(load().ust_get_counts(self._h, p, dev), self._h)
@@ -226,6 +237,7 @@ class USTBatch:
     tau = UST.tau
     _out = UST._out
     diag = UST.diag
+    centralities = UST.centralities
     counts = UST.counts
     column = UST.column
     info = UST.info

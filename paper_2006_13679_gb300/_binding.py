@@ -70,6 +70,8 @@ _SIGNATURES = {
     "ust_reset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "ust_sample_aggregate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]),
     "ust_set_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "ust_centralities": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int32]),
     "ust_diag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int32]),
     "ust_tau": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_double]),
     "ust_get_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),

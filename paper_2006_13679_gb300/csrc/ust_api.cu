@@ -322,6 +322,36 @@ int ust_diag(ust_ctx *h, double eps, double *diag_out, int32_t out_on_device)
     return UST_OK;
 }
 
+int ust_centralities(ust_ctx *h, double eps, double *closeness_out, double *nrwb_out, double *kirchhoff_out,
+                     int32_t out_on_device)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    const int count = c->batch ? c->batch : 1;
+    // the diagonal goes to solver scratch that is free once the column is known
+    double *d_diag = c->batch ? c->d_br64 : c->d_f64 + c->n;
+    int rc = ust_diag(h, eps, d_diag, 1);
+    if (rc) return rc;
+    if (!closeness_out && !nrwb_out && !kirchhoff_out) return UST_OK;
+    const size_t n = (size_t)c->n;
+    double *dc = closeness_out, *dn = nrwb_out, *dk = kirchhoff_out, *tmp = nullptr;
+    if (!out_on_device) {
+        if (cudaMalloc(&tmp, (2 * n + (size_t)count) * sizeof(double)) != cudaSuccess)
+            return ust::fail(c, UST_ENOMEM, "centrality outputs");
+        dc = closeness_out ? tmp : nullptr;
+        dn = nrwb_out ? tmp + n : nullptr;
+        dk = kirchhoff_out ? tmp + 2 * n : nullptr;
+    }
+    rc = ust::run_centralities(c, c->batch ? c->d_comb : nullptr, count, d_diag, dc, dn, dk);
+    if (!rc && !out_on_device) {
+        if (closeness_out) rc = copy_out(c, closeness_out, dc, n * sizeof(double), 0);
+        if (!rc && nrwb_out) rc = copy_out(c, nrwb_out, dn, n * sizeof(double), 0);
+        if (!rc && kirchhoff_out) rc = copy_out(c, kirchhoff_out, dk, (size_t)count * sizeof(double), 0);
+    }
+    cudaFree(tmp);
+    return rc;
+}
+
 int ust_get_counts(ust_ctx *h, int64_t *R_out, int32_t out_on_device)
 {
     if (!h) return UST_EINVAL;

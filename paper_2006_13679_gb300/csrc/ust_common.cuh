@@ -225,6 +225,10 @@ int run_batch_prepare(Ctx *c, const PrepDesc *d_desc, int count, int *d_out);
 // B_u, ecc, f^c(u) and (when they fit path_cap) the paths of one graph in one
 // CTA; d_out: status, ecc, f^c(u).
 int run_prepare_single(Ctx *c, const PrepDesc &d, int *d_out);
+// Closeness, random-walk betweenness and Kirchhoff index from diagonals
+// (d_graphs: one CombineDesc per graph, or NULL for the context's single graph).
+int run_centralities(Ctx *c, const CombineDesc *d_graphs, int count, const double *d_diag, double *d_closeness,
+                     double *d_nrwb, double *d_kirchhoff);
 // Single graphs up to this many vertices get B_u from one CTA in one launch
 // (f^c(u) < n^2 / 2 stays below 2^31).
 constexpr int kPrepMaxN = 32768;

@@ -100,3 +100,18 @@ def test_batch_of_256_uneven_graphs(pkg, orc):
             assert ok
             assert np.max(np.abs(x[i] - x_ref)) <= 1e-8 * max(1.0, float(np.max(np.abs(x_ref)))), i
             np.testing.assert_allclose(d[i], orc.combine(R[i], 1024, x[i], piv[i]), rtol=1e-12, atol=0)
+
+
+def test_batch_centralities(pkg, orc):
+    gs = [synth.grid(6, 6), synth.ba(2000, 4, seed=3), synth.cycle(40)]
+    piv = [14, synth.max_degree_vertex(gs[1]), 0]
+    with pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], piv) as b:
+        b.sample_aggregate(300, 4)
+        d = b.split(b.diag())
+        c = b.centralities()
+        cl, nr = b.split(c["closeness"]), b.split(c["nrwb"])
+        for i in range(len(gs)):
+            ref = orc.centralities(d[i])
+            np.testing.assert_allclose(cl[i], ref["closeness"], rtol=1e-12, atol=0)
+            np.testing.assert_allclose(nr[i], ref["nrwb"], rtol=1e-12, atol=0)
+            assert abs(c["kirchhoff"][i] - ref["kirchhoff"]) <= 1e-12 * abs(ref["kirchhoff"])

@@ -325,3 +325,18 @@ def test_batch_input_checks_name_the_graph(pkg):
         pkg.USTBatch([(good.row_ptr, good.col_idx), (bad_rp, bad_ci)], [0, 0])
     assert e.value.code == pkg.UST_EINVAL
     assert "graph 1" in str(e.value)
+
+
+@pytest.mark.parametrize("name", ["grid48", "rmat12"])
+def test_centralities_from_the_diagonal(pkg, orc, name):
+    """ust_centralities: closeness, NRWB and Kirchhoff index of the estimated
+    diagonal equal the oracle's formulas applied to the same diagonal."""
+    g, u = GRAPHS[name]()
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(400, 3)
+        d = h.diag()
+        c = h.centralities()
+    ref = orc.centralities(d)
+    np.testing.assert_allclose(c["closeness"], ref["closeness"], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(c["nrwb"], ref["nrwb"], rtol=1e-12, atol=0)
+    assert abs(c["kirchhoff"] - ref["kirchhoff"]) <= 1e-12 * abs(ref["kirchhoff"])

@@ -356,3 +356,52 @@ def test_estimate_closed_form_cycle(orc):
     k = np.arange(n)
     # per-tree count for vertex k is in {k - (n - k), k} ... bounded by n
     np.testing.assert_allclose(R / tau, k * (n - k) / n, atol=5 * n / math.sqrt(tau))
+
+
+# ---------------------------------------------------------------- centralities
+
+def test_farness_from_diagonal_equals_sum_of_resistances():
+    """Eq. elec-farness: sum_w r(v, w) = n L+[v,v] + tr(L+), checked against
+    effective resistances summed pair by pair from the dense pseudoinverse."""
+    import oracle
+    for g in small_graphs():
+        Lp = oracle.dense_pinv(g)
+        d = np.diag(Lp)
+        R = d[:, None] + d[None, :] - 2 * Lp  # Eq. eff-res, every pair
+        c = oracle.centralities(d)
+        np.testing.assert_allclose(c["farness"], R.sum(axis=1), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(c["closeness"], (g.n - 1) / R.sum(axis=1), rtol=1e-12)
+        # Kirchhoff index: the sum of r over unordered pairs (Klein and Randic)
+        assert math.isclose(c["kirchhoff"], R.sum() / 2, rel_tol=1e-12)
+
+
+def test_centralities_closed_forms():
+    import oracle
+    for n in (5, 8, 13):
+        c = oracle.centralities(np.diag(oracle.dense_pinv(synth.complete(n))))
+        np.testing.assert_allclose(c["closeness"], n / 2, rtol=1e-12)      # r = 2/n to the n-1 others
+        assert math.isclose(c["kirchhoff"], n - 1, rel_tol=1e-12)
+        np.testing.assert_allclose(c["nrwb"], 1 / n + 1 / (2 * (n - 1)), rtol=1e-12)
+        c = oracle.centralities(np.diag(oracle.dense_pinv(synth.cycle(n))))
+        np.testing.assert_allclose(c["closeness"], 6 / (n + 1), rtol=1e-12)  # sum_k k(n-k)/n = (n^2-1)/6
+        assert math.isclose(c["kirchhoff"], n * (n * n - 1) / 12, rel_tol=1e-12)
+        c = oracle.centralities(np.diag(oracle.dense_pinv(synth.star(n))))
+        assert math.isclose(c["kirchhoff"], (n - 1) ** 2, rel_tol=1e-12)   # n-1 pairs at 1, the rest at 2
+
+
+def test_nrwb_equals_ratio_of_sums_over_inverse_of_L_plus_P():
+    """The NRWB lemma against its derivation, computed straight from
+    M^{-1} = (L + J/n)^{-1}: 1/n + (sum_t M_tt - M_tv) / ((n-1) sum_t (M_tt + M_vv - 2 M_tv))."""
+    import oracle
+    for g in small_graphs() + [synth.star(6), synth.path(7)]:
+        n = g.n
+        L = oracle.laplacian(g)
+        M1 = np.linalg.inv(L + np.ones((n, n)) / n)
+        ref = np.empty(n)
+        for v in range(n):
+            t = np.arange(n) != v
+            num = np.sum(M1[t, t] - M1[t, v])
+            den = np.sum(M1[t, t] + M1[v, v] - 2 * M1[t, v])
+            ref[v] = 1.0 / n + num / ((n - 1) * den)
+        c = oracle.centralities(np.diag(oracle.dense_pinv(g)))
+        np.testing.assert_allclose(c["nrwb"], ref, rtol=1e-10, atol=1e-12)
