@@ -207,6 +207,21 @@ UST_API int64_t ust_tau(const ust_ctx *c, double eps);
 /* R[v] as exact integers (n int64). */
 UST_API int ust_get_counts(ust_ctx *c, int64_t *R_out, int32_t out_on_device);
 
+/* Turns counting of tree arcs on (on != 0, counts start at 0) or off. While
+ * on, every tree sampled by ust_sample_aggregate adds 1 at the CSR position
+ * k of each of its arcs v -> parent(v) (the final stack entry of v). The
+ * fraction of trees that use an undirected edge {v, w} (both arcs summed) is
+ * an estimate of Pr[e in UST] = r(v, w) (Kirchhoff; Appendix on Kirchhoff
+ * edge centrality, sampling USTs and counting the trees an edge appears in).
+ * Costs one Philox draw and one atomic per vertex and tree. Errors:
+ * UST_ENOMEM. */
+UST_API int ust_track_edges(ust_ctx *c, int32_t on);
+
+/* The arc counts (nnz int64, CSR order; a batch: all graphs' arcs one after
+ * another). Committed with R: a failed call leaves them unchanged;
+ * ust_reset clears them. Errors: UST_ESTATE when counting is off. */
+UST_API int ust_get_edge_counts(ust_ctx *c, int64_t *counts_out, int32_t out_on_device);
+
 /* The column x = L^+[:, u] (n doubles); solves it first if needed. */
 UST_API int ust_get_column(ust_ctx *c, double *x_out, int32_t out_on_device);
 

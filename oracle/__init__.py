@@ -197,6 +197,34 @@ def combine(R: np.ndarray, tau: int, x: np.ndarray, u: int) -> np.ndarray:
     return d
 
 
+def tree_arcs(g, nxt, u: int) -> np.ndarray:
+    """CSR positions of a rooted tree's arcs v -> next[v], v != u (rows are
+    sorted, so the position is found by binary search in row v)."""
+    rp, ci = _csr(g)
+    out = np.empty(g.n - 1, dtype=np.int64)
+    k = 0
+    for v in range(g.n):
+        if v == u:
+            continue
+        row = ci[rp[v]:rp[v + 1]]
+        j = int(np.searchsorted(row, nxt[v]))
+        assert j < row.shape[0] and row[j] == nxt[v], "tree arc not in the graph"
+        out[k] = rp[v] + j
+        k += 1
+    return out
+
+
+def edge_counts(g, u: int, t0: int, t1: int, seed: int, graph: int = 0) -> np.ndarray:
+    """Per CSR arc v -> w, the number of trees t0 .. t1-1 (Wilson's loop-erased
+    walks, Appendix A.2) in which w is v's parent: sampling USTs and counting
+    the trees each edge appears in (appendix on Kirchhoff edge centrality)."""
+    counts = np.zeros(g.nnz, dtype=np.int64)
+    for t in range(t0, t1):
+        nxt, _, _ = wilson(g, u, t, seed, graph)
+        np.add.at(counts, tree_arcs(g, nxt, u), 1)
+    return counts
+
+
 def centralities(diag) -> dict:
     """Centralities from a diagonal of L^+, written out from the paper:
     electrical farness f(v) = n L+[v,v] + tr(L+) (Section 3.1, Eq.

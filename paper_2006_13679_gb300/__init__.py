@@ -141,6 +141,16 @@ class UST:
                                       ctypes.c_void_p(nr.ctypes.data), ctypes.c_void_p(kf.ctypes.data), 0), self._h)
         return {"closeness": cl, "nrwb": nr, "kirchhoff": kf if count > 1 else float(kf[0])}
 
+    def track_edges(self, on: bool = True) -> None:
+        """Counts, per CSR arc v -> w, the sampled trees in which w is v's parent."""
+        check(load().ust_track_edges(self._h, int(bool(on))), self._h)
+
+    def edge_counts(self, out=None):
+        nnz = getattr(self, "nnz", None) or int(self.info()["nnz"])
+        out, ptr, dev = self._out(out, np.int64, nnz)
+        check(load().ust_get_edge_counts(self._h, ptr, dev), self._h)
+        return out
+
     def counts(self, out=None):
         out, p, dev = self._out(out, np.int64, self.n)
         check(load().ust_get_counts(self._h, p, dev), self._h)
@@ -238,6 +248,8 @@ class USTBatch:
     _out = UST._out
     diag = UST.diag
     centralities = UST.centralities
+    track_edges = UST.track_edges
+    edge_counts = UST.edge_counts
     counts = UST.counts
     column = UST.column
     info = UST.info

@@ -75,6 +75,8 @@ _SIGNATURES = {
     "ust_diag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int32]),
     "ust_tau": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_double]),
     "ust_get_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "ust_track_edges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "ust_get_edge_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "ust_get_column": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "ust_get_bfs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ust_tree_range_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,

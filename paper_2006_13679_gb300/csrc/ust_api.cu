@@ -50,6 +50,8 @@ void release(Ctx *c)
     cudaFree(c->d_comb);
     cudaFree(c->d_prep);
     cudaFree(c->d_tasks);
+    cudaFree(c->d_ecount);
+    cudaFree(c->d_ecount_tmp);
     cudaFree(c->d_results);
     cudaFreeHost(c->h_results);
     cudaFree(c->d_bw32);
@@ -260,6 +262,7 @@ int ust_reset(ust_ctx *h, int32_t pivot)
     c->max_depth_seen = 0;
     c->x_valid = false;
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * 8, c->stream));
+    if (c->d_ecount) UST_CUDA_TRY(cudaMemsetAsync(c->d_ecount, 0, (size_t)c->nnz * 8, c->stream));
     return ust::run_bfs(c);
 }
 
@@ -271,12 +274,16 @@ int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
     if (n_trees == 0) return UST_OK;
     if (c->batch) return ust::batch_sample_aggregate(c, n_trees, seed);
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_Rtmp, c->d_R, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->d_ecount)
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_ecount_tmp, c->d_ecount, (size_t)c->nnz * 8, cudaMemcpyDeviceToDevice,
+                                     c->stream));
     int64_t draws = 0, rounds = 0;
     int max_rounds = 0, max_depth = 0;
     const int rc = ust::run_sampler(c, c->trees, c->trees + n_trees, seed, c->d_Rtmp, nullptr, nullptr, &draws,
                                     &rounds, &max_rounds, &max_depth);
     if (rc) return rc;
     std::swap(c->d_R, c->d_Rtmp);
+    std::swap(c->d_ecount, c->d_ecount_tmp);
     c->trees += n_trees;
     c->seed = seed;
     c->draws += draws;
@@ -350,6 +357,33 @@ int ust_centralities(ust_ctx *h, double eps, double *closeness_out, double *nrwb
     }
     cudaFree(tmp);
     return rc;
+}
+
+int ust_track_edges(ust_ctx *h, int32_t on)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    cudaFree(c->d_ecount);
+    cudaFree(c->d_ecount_tmp);
+    c->d_ecount = c->d_ecount_tmp = nullptr;
+    if (!on) return UST_OK;
+    const size_t bytes = (size_t)c->nnz * sizeof(int64_t);
+    if (cudaMalloc(&c->d_ecount, bytes) != cudaSuccess || cudaMalloc(&c->d_ecount_tmp, bytes) != cudaSuccess) {
+        cudaFree(c->d_ecount);
+        c->d_ecount = nullptr;
+        return ust::fail(c, UST_ENOMEM, "arc counts");
+    }
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_ecount, 0, bytes, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return UST_OK;
+}
+
+int ust_get_edge_counts(ust_ctx *h, int64_t *counts_out, int32_t out_on_device)
+{
+    if (!h) return UST_EINVAL;
+    Ctx *c = &h->c;
+    if (!c->d_ecount) return ust::fail(c, UST_ESTATE, "arc counting is off (ust_track_edges)");
+    return copy_out(c, counts_out, c->d_ecount, (size_t)c->nnz * sizeof(int64_t), out_on_device);
 }
 
 int ust_get_counts(ust_ctx *h, int64_t *R_out, int32_t out_on_device)

@@ -46,6 +46,7 @@ GraphDesc desc_of(const Ctx *c, int g, long long tree_begin)
     d.pchild = c->d_path + c->path_cap + c->bpoff[g];
     d.powner = c->d_path + 2 * c->path_cap + c->bpoff[g];
     d.fc = (int)c->bfarness[g];
+    d.aoff = c->baoff[g];
     return d;
 }
 
@@ -130,6 +131,9 @@ int batch_sample(Ctx *c, const std::vector<int64_t> &count, uint64_t seed)
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_items, starts.data(), starts.size() * sizeof(long long), cudaMemcpyHostToDevice,
                                  c->stream));
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_Rtmp, c->d_R, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->d_ecount)
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_ecount_tmp, c->d_ecount, (size_t)c->nnz * 8, cudaMemcpyDeviceToDevice,
+                                     c->stream));
     int64_t draws_total = 0, rounds_total = 0;
     phase_open(c, Ctx::kEvSample);  // both launches in one timed phase
     for (int k = 0; k < kNumClasses; ++k) {
@@ -151,6 +155,7 @@ int batch_sample(Ctx *c, const std::vector<int64_t> &count, uint64_t seed)
     }
     phase_close(c, Ctx::kEvSample);
     std::swap(c->d_R, c->d_Rtmp);
+    std::swap(c->d_ecount, c->d_ecount_tmp);
     int64_t trees = 0;
     for (int g = 0; g < B; ++g) {
         if (count[g] > 0) c->btrees[g] += count[g];
@@ -340,6 +345,7 @@ int batch_reset(Ctx *c)
     c->x_valid = false;
     std::fill(c->btrees.begin(), c->btrees.end(), 0);
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * 8, c->stream));
+    if (c->d_ecount) UST_CUDA_TRY(cudaMemsetAsync(c->d_ecount, 0, (size_t)c->nnz * 8, c->stream));
     return batch_prepare(c, true);
 }
 

@@ -40,6 +40,7 @@ struct GraphDesc {
     // P(powner[p]); fc = f^c(u) entries
     const int32_t *pchild, *powner;
     int fc;
+    long long aoff;  // offset of the graph's arcs in batch-wide arc arrays
 };
 
 // Graphs of at most this many vertices run the sampler with its per-tree
@@ -123,6 +124,8 @@ struct Ctx {
     int32_t *d_Rp = nullptr;    // ctas * n partial counts (single graph)
     int64_t *d_R = nullptr;     // committed counts
     int64_t *d_Rtmp = nullptr;  // scratch counts (uncommitted)
+    int64_t *d_ecount = nullptr;     // trees using each arc v -> parent(v) (ust_track_edges), committed
+    int64_t *d_ecount_tmp = nullptr; // the same while a call runs
     int64_t *d_stats = nullptr; // [0] draws, [1] rounds, [2] max rounds, [3] max depth, [4] next tree, [5] status
     int64_t *h_stats = nullptr; // pinned mirror
 

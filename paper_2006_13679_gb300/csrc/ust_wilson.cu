@@ -83,6 +83,7 @@ struct SampleParams {
     int max_rounds, max_steps;
     int mode;  // 0: aggregate, 1: export trees
     int32_t *next_out, *pops_out;  // mode 1: item i's tree at [i n, (i + 1) n)
+    unsigned long long *edge_counts;  // when set: +1 per tree at every arc v -> parent(v) (index aoff + arc)
     unsigned long long *R_direct;   // when set, counts go to R_direct[voff + v] (batches)
 };
 
@@ -469,6 +470,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
             my_draws += s_draws;
             my_rounds += (unsigned long long)rounds;
             my_max_rounds = max(my_max_rounds, rounds);
+        }
+        if (p.edge_counts) {  // the tree's arcs v -> parent(v): the final stack entry of every v
+            for (int v = tid; v < n; v += BT) {
+                if (v == u) continue;
+                const int b = __ldg(gd.rp + v), e = __ldg(gd.rp + v + 1);
+                const unsigned long long x = philox_x64((uint32_t)v, (uint32_t)pop[v], tree, gd.graph, p.key0, p.key1);
+                atomicAdd(p.edge_counts + gd.aoff + b + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
+            }
         }
 
         if (p.mode == 1) {
@@ -1085,6 +1094,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             my_rounds += (unsigned long long)rounds;
             my_max_rounds = max(my_max_rounds, rounds);
         }
+        if (p.edge_counts) {  // the tree's arcs v -> parent(v): the final stack entry of every v
+            for (int v = tid; v < n; v += BT) {
+                if (v == u) continue;
+                const int b = __ldg(gd.rp + v), e = __ldg(gd.rp + v + 1);
+                const unsigned long long x = philox_x64((uint32_t)v, (uint32_t)pop[v], tree, gd.graph, p.key0, p.key1);
+                atomicAdd(p.edge_counts + gd.aoff + b + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
+            }
+        }
 
         if (p.mode == 1) {
             const long long o = s_tree * (long long)n;
@@ -1571,6 +1588,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     gd.pchild = c->d_path + c->path_cap;
     gd.powner = c->d_path + 2 * c->path_cap;
     gd.fc = (int)c->farness;
+    gd.aoff = 0;
     const GraphDesc &o = c->single_desc;
     const bool same = o.n == gd.n && o.u == gd.u && o.graph == gd.graph && o.rp == gd.rp && o.ci == gd.ci &&
                       o.bpar == gd.bpar && o.path == gd.path && o.pathptr == gd.pathptr && o.pchild == gd.pchild &&
@@ -1595,6 +1613,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     p.ws = c->d_ws;
     p.stride = c->ws_stride;
     p.Rp = c->d_Rp;
+    p.edge_counts = (mode == 0) ? reinterpret_cast<unsigned long long *>(c->d_ecount_tmp) : nullptr;
     unsigned long long *st = reinterpret_cast<unsigned long long *>(c->d_stats);
     p.next_tree = st + 4;
     p.stats = st;
@@ -1801,6 +1820,7 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
         d.pchild = pchild;
         d.powner = powner;
         d.fc = 0;  // set below, once f^c(u) is known
+        d.aoff = 0;
         *desc = d;
         item_start[0] = 0;
         item_start[1] = kOpenEnd;
@@ -1997,6 +2017,7 @@ int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, c
     p.item_start = d_item_start;
     p.total_items = total_items;
     p.R_direct = reinterpret_cast<unsigned long long *>(d_R);
+    p.edge_counts = reinterpret_cast<unsigned long long *>(c->d_ecount_tmp);
     const int grid = (int)std::min<long long>(cfg.ctas, total_items);
     phase_begin(c, Ctx::kEvSample);
     const cudaError_t e = launch_shape(cfg, grid, c->stream, p);

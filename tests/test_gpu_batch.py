@@ -115,3 +115,16 @@ def test_batch_centralities(pkg, orc):
             np.testing.assert_allclose(cl[i], ref["closeness"], rtol=1e-12, atol=0)
             np.testing.assert_allclose(nr[i], ref["nrwb"], rtol=1e-12, atol=0)
             assert abs(c["kirchhoff"][i] - ref["kirchhoff"]) <= 1e-12 * abs(ref["kirchhoff"])
+
+
+def test_batch_edge_counts(pkg, orc):
+    gs = [synth.grid(6, 6), synth.ba(2000, 4, seed=3), synth.er(1500, 6.0, seed=5)]
+    piv = [14, synth.max_degree_vertex(gs[1]), synth.max_degree_vertex(gs[2])]
+    with pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], piv, graph_id=5) as b:
+        b.track_edges(True)
+        b.sample_aggregate(40, 6)
+        got = b.edge_counts()
+        off = 0
+        for i, g in enumerate(gs):
+            assert np.array_equal(got[off:off + g.nnz], orc.edge_counts(g, piv[i], 0, 40, 6, graph=5 + i)), i
+            off += g.nnz

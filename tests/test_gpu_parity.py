@@ -340,3 +340,32 @@ def test_centralities_from_the_diagonal(pkg, orc, name):
     np.testing.assert_allclose(c["closeness"], ref["closeness"], rtol=1e-12, atol=0)
     np.testing.assert_allclose(c["nrwb"], ref["nrwb"], rtol=1e-12, atol=0)
     assert abs(c["kirchhoff"] - ref["kirchhoff"]) <= 1e-12 * abs(ref["kirchhoff"])
+
+
+@pytest.mark.parametrize("name,trees", [("grid48", 120), ("rmat12", 200), ("ba70000", 6)])
+def test_edge_counts_bit_exact(pkg, orc, name, trees):
+    """ust_track_edges: per-arc tree counts equal the oracle's, in both the
+    shared-memory and the global-memory sampler."""
+    if name == "ba70000":
+        g = synth.ba(70000, 3, seed=9)
+        u = synth.max_degree_vertex(g)
+    else:
+        g, u = GRAPHS[name]()
+    with make(pkg, g, u) as h:
+        h.track_edges(True)
+        h.sample_aggregate(trees // 2, 13)
+        h.sample_aggregate(trees - trees // 2, 13)
+        got = h.edge_counts()
+        assert got.sum() == trees * (g.n - 1)
+        assert np.array_equal(got, orc.edge_counts(g, u, 0, trees, 13))
+        if name == "grid48":
+            with pytest.raises(pkg.UstError):
+                h2 = make(pkg, g, u, max_pop_rounds=1)
+                h2.track_edges(True)
+                try:
+                    h2.sample_aggregate(4, 0)
+                finally:
+                    assert not h2.edge_counts().any()  # a failed call leaves the counts unchanged
+                    h2.close()
+            h.reset(u)
+            assert not h.edge_counts().any()

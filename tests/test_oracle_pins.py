@@ -405,3 +405,53 @@ def test_nrwb_equals_ratio_of_sums_over_inverse_of_L_plus_P():
             ref[v] = 1.0 / n + num / ((n - 1) * den)
         c = oracle.centralities(np.diag(oracle.dense_pinv(g)))
         np.testing.assert_allclose(c["nrwb"], ref, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- edge counts
+
+def _undirected(g, arc_values):
+    """Sum of both arcs of every undirected edge, keyed by (a, b), a < b."""
+    rp, ci = g.row_ptr, g.col_idx
+    out = {}
+    for v in range(g.n):
+        for k in range(rp[v], rp[v + 1]):
+            w = int(ci[k])
+            key = (min(v, w), max(v, w))
+            out[key] = out.get(key, 0) + arc_values[k]
+    return out
+
+
+def test_edge_frequency_over_all_spanning_trees_is_effective_resistance():
+    """Kirchhoff: the fraction of all spanning trees that contain e equals
+    r(e). The oracle's arc extraction applied to every enumerated tree (rooted
+    at each pivot) reproduces the dense-pinv resistances exactly."""
+    import oracle
+    for g in tiny_graphs():
+        Lp = oracle.dense_pinv(g)
+        trees = oracle.spanning_trees(g)
+        for u in (0, g.n - 1):
+            counts = np.zeros(g.nnz, dtype=np.int64)
+            for te in trees:
+                np.add.at(counts, oracle.tree_arcs(g, oracle.root_tree(te, g.n, u), u), 1)
+            assert counts.sum() == len(trees) * (g.n - 1)
+            for (a, b), c in _undirected(g, counts).items():
+                r = Lp[a, a] + Lp[b, b] - 2 * Lp[a, b]
+                assert abs(c / len(trees) - r) <= 1e-12, (g.name, a, b)
+
+
+def test_sampled_edge_frequencies_match_resistances():
+    """Sampled trees: every tree has n-1 arcs, bridges are in every tree, and
+    edge frequencies are within 5 standard errors of r(e)."""
+    import oracle
+    g = synth.from_edges(8, [0, 1, 2, 0, 3, 4, 5, 6, 5], [1, 2, 0, 3, 4, 5, 6, 7, 7], name="two-blocks")
+    T = 3000
+    counts = oracle.edge_counts(g, 0, 0, T, seed=4)
+    assert counts.sum() == T * (g.n - 1)
+    Lp = oracle.dense_pinv(g)
+    for (a, b), c in _undirected(g, counts).items():
+        r = Lp[a, a] + Lp[b, b] - 2 * Lp[a, b]
+        f = c / T
+        if abs(r - 1.0) < 1e-12:
+            assert c == T  # a bridge is in every spanning tree
+        sigma = math.sqrt(max(r * (1 - r), 1e-12) / T)
+        assert abs(f - r) <= 5 * sigma + 1e-12, (a, b, f, r)
