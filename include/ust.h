@@ -143,6 +143,19 @@ UST_API void ust_default_opts(ust_opts *o);
  * UST_ECUDA. On error *out is NULL. */
 UST_API int ust_init(const ust_csr *g, int32_t pivot, const ust_opts *o, ust_ctx **out);
 
+/* A pivot of low eccentricity (Appendix D, choice of u; Theorem 1's running
+ * time grows with ecc(u)^2): `sweeps` BFS runs (<= 0: the paper's 10), the
+ * first from `start` (< 0: the vertex of largest degree), each next one
+ * from the vertex farthest from the previous source. Every vertex keeps the
+ * largest distance seen from any source, a lower bound on its
+ * eccentricity; *pivot_out is the vertex of least bound, *bound_out (may be
+ * NULL) that bound. Ties go to the smallest vertex id. The graph is checked
+ * as in ust_init (host or device arrays, not modified). Errors: UST_EINVAL,
+ * UST_ENOTCONNECTED, UST_ENOMEM, UST_ECUDA; the message is
+ * ust_last_error(NULL). */
+UST_API int ust_select_pivot(const ust_csr *g, int32_t sweeps, int32_t start, void *stream, int32_t *pivot_out,
+                             int32_t *bound_out);
+
 /* Creates a context for a batch of `count` graphs gs[0..count), graph g with
  * pivot pivots[g] (Algorithm 1 for every graph at once). The graphs'
  * vertices are laid out one after another: every per-vertex output (counts,

@@ -197,6 +197,25 @@ def combine(R: np.ndarray, tau: int, x: np.ndarray, u: int) -> np.ndarray:
     return d
 
 
+def select_pivot(g, sweeps: int = 10, start: int = -1):
+    """Pivot of low eccentricity (Appendix D, choice of u): BFS from a first
+    source (start, or the vertex of largest degree), then from the vertex
+    farthest from the previous source, `sweeps` times; each vertex keeps the
+    largest distance seen, a lower bound on its eccentricity. Returns the
+    vertex of least bound and the bound. Ties: smallest vertex id."""
+    deg = np.diff(np.asarray(g.row_ptr, dtype=np.int64))
+    s = int(np.argmax(deg)) if start < 0 else int(start)
+    lb = np.zeros(g.n, dtype=np.int64)
+    for _ in range(sweeps):
+        _, dist, _ = bfs(g, s)
+        if (dist < 0).any():
+            raise ValueError("graph is not connected")
+        lb = np.maximum(lb, dist)
+        s = int(np.argmax(dist))
+    piv = int(np.argmin(lb))
+    return piv, int(lb[piv])
+
+
 def tree_arcs(g, nxt, u: int) -> np.ndarray:
     """CSR positions of a rooted tree's arcs v -> next[v], v != u (rows are
     sorted, so the position is found by binary search in row v)."""

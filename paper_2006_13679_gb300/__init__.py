@@ -17,7 +17,7 @@ from ._binding import (UST_EINVAL, UST_ENOMEM, UST_ENOTCONNECTED, UST_ENOTCONVER
                        UST_ETIMEOUT, UST_OK, UstError, check, load)
 from ._build import LIB as LIB_PATH
 
-__all__ = ["UST", "USTBatch", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
+__all__ = ["UST", "USTBatch", "select_pivot", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
            "UST_ENOMEM", "UST_ETIMEOUT", "UST_ENOTCONVERGED", "UST_ESTATE"]
 
 
@@ -51,6 +51,21 @@ def _stream_handle(stream):
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
+
+
+def select_pivot(row_ptr, col_idx, sweeps: int = 10, start: int = -1, stream=None) -> tuple[int, int]:
+    """``ust_select_pivot``: (pivot, eccentricity lower bound) by double sweeps."""
+    L = load()
+    rp = row_ptr if _is_torch(row_ptr) else np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = col_idx if _is_torch(col_idx) else np.ascontiguousarray(col_idx, dtype=np.int32)
+    prp, dev = _ptr(rp, np.int32)
+    pci, _ = _ptr(ci, np.int32)
+    g = _binding.ust_csr(n=int(rp.shape[0]) - 1, nnz=int(ci.shape[0]), row_ptr=prp.value, col_idx=pci.value,
+                         on_device=dev)
+    sh = _stream_handle(stream)
+    piv, bound = ctypes.c_int32(), ctypes.c_int32()
+    check(L.ust_select_pivot(ctypes.byref(g), int(sweeps), int(start), sh, ctypes.byref(piv), ctypes.byref(bound)))
+    return int(piv.value), int(bound.value)
 
 
 class UST:

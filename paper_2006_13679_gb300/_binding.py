@@ -64,6 +64,8 @@ _SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_void_p)]),
     "ust_init_batch": (ctypes.c_int, [ctypes.POINTER(ust_csr), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                       ctypes.POINTER(ust_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "ust_select_pivot": (ctypes.c_int, [ctypes.POINTER(ust_csr), ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "ust_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
     "ust_batch_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ust_batch_graph_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ust_info)]),

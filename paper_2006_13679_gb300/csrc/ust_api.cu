@@ -216,6 +216,49 @@ int ust_init_batch(const ust_csr *gs, const int32_t *pivots, int32_t count, cons
     return UST_OK;
 }
 
+int ust_select_pivot(const ust_csr *g, int32_t sweeps, int32_t start, void *stream, int32_t *pivot_out,
+                     int32_t *bound_out)
+{
+    if (!g || !g->row_ptr || !g->col_idx || g->n < 2 || g->nnz < 2 || !pivot_out || start >= g->n) {
+        g_init_error = "invalid graph, start vertex or output (need n >= 2, nnz >= 2, start < n)";
+        return UST_EINVAL;
+    }
+    Ctx c;
+    c.n = g->n;
+    c.nnz = g->nnz;
+    c.stream = reinterpret_cast<cudaStream_t>(stream);
+    int rc = UST_OK;
+    int32_t *rp = const_cast<int32_t *>(g->row_ptr), *ci = const_cast<int32_t *>(g->col_idx);
+    int32_t *own_rp = nullptr, *own_ci = nullptr, pivot = -1, bound = 0;
+    int *d_bad = nullptr;
+    if (cudaGetDevice(&c.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
+        cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) {
+        rc = ust::fail(&c, UST_ECUDA, "device set-up");
+    }
+    if (!rc && !g->on_device) {
+        if (cudaMalloc(&own_rp, ((size_t)g->n + 1) * 4) != cudaSuccess ||
+            cudaMalloc(&own_ci, (size_t)g->nnz * 4) != cudaSuccess ||
+            cudaMemcpyAsync(own_rp, g->row_ptr, ((size_t)g->n + 1) * 4, cudaMemcpyHostToDevice, c.stream) != cudaSuccess ||
+            cudaMemcpyAsync(own_ci, g->col_idx, (size_t)g->nnz * 4, cudaMemcpyHostToDevice, c.stream) != cudaSuccess)
+            rc = ust::fail(&c, UST_ENOMEM, "device copy of the graph");
+        rp = own_rp;
+        ci = own_ci;
+    }
+    if (!rc) rc = ust::check_graph(&c, g->n, g->nnz, rp, ci, d_bad);
+    if (!rc) rc = ust::select_pivot(&c, g->n, rp, ci, sweeps > 0 ? sweeps : 10, start, &pivot, &bound);
+    cudaFree(own_rp);
+    cudaFree(own_ci);
+    cudaFree(d_bad);
+    if (rc) {
+        g_init_error = c.err;
+        return rc;
+    }
+    *pivot_out = pivot;
+    if (bound_out) *bound_out = bound;
+    return UST_OK;
+}
+
 int32_t ust_batch_size(const ust_ctx *h)
 {
     return h ? h->c.batch : 0;

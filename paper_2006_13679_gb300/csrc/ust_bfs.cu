@@ -170,7 +170,135 @@ __global__ void check_arcs_kernel(int n, int nnz, const int32_t *__restrict__ rp
     if (flags) atomicOr(bad, flags);
 }
 
+// ---------------------------------------------------------------------------
+// Pivot selection (Appendix D, choice of u): eccentricity lower bounds from
+// repeated double sweeps. Packed keys make the reductions single atomics
+// with the smallest id winning ties.
+__global__ void max_degree_kernel(int n, const int32_t *__restrict__ rp, unsigned long long *best)
+{
+    unsigned long long b = 0ull;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const unsigned long long k = ((unsigned long long)(uint32_t)(__ldg(rp + v + 1) - __ldg(rp + v)) << 32) |
+                                     (uint32_t)(0x7FFFFFFF - v);
+        b = k > b ? k : b;
+    }
+    atomicMax(best, b);
+}
+
+// lb = max(lb, dist); *far = the farthest vertex; *bad |= 1 for unreached vertices
+__global__ void sweep_update_kernel(int n, const int32_t *__restrict__ dist, int32_t *lb, unsigned long long *far,
+                                    int *bad)
+{
+    unsigned long long b = 0ull;
+    int unreached = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int d = dist[v];
+        if (d < 0) {
+            unreached = 1;
+            continue;
+        }
+        if (d > lb[v]) lb[v] = d;
+        const unsigned long long k = ((unsigned long long)(uint32_t)d << 32) | (uint32_t)(0x7FFFFFFF - v);
+        b = k > b ? k : b;
+    }
+    atomicMax(far, b);
+    if (unreached) atomicOr(bad, 1);
+}
+
+__global__ void min_bound_kernel(int n, const int32_t *__restrict__ lb, unsigned long long *best)
+{
+    unsigned long long b = ~0ull;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const unsigned long long k = ((unsigned long long)(uint32_t)lb[v] << 32) | (uint32_t)v;
+        b = k < b ? k : b;
+    }
+    atomicMin(best, b);
+}
+
 }  // namespace
+
+int select_pivot(Ctx *c, int n, const int32_t *d_rp, const int32_t *d_ci, int sweeps, int start, int32_t *pivot,
+                 int32_t *bound)
+{
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    int32_t *d_dist = nullptr, *d_bpar = nullptr, *d_lb = nullptr;
+    unsigned long long *d_words = nullptr;  // [0] packed key, [1] BFS flag and unreached flag
+    auto release = [&]() {
+        cudaFree(d_dist);
+        cudaFree(d_bpar);
+        cudaFree(d_lb);
+        cudaFree(d_words);
+    };
+    if (cudaMalloc(&d_dist, (size_t)n * 4) != cudaSuccess || cudaMalloc(&d_bpar, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&d_lb, (size_t)n * 4) != cudaSuccess || cudaMalloc(&d_words, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        release();
+        return fail(c, UST_ENOMEM, "pivot selection buffers");
+    }
+    int rc = UST_OK;
+    unsigned long long key = 0ull;
+    int32_t h_flag = 0;
+    int32_t *d_flag = reinterpret_cast<int32_t *>(d_words + 1);
+    int *d_bad = reinterpret_cast<int *>(d_words + 2);
+#define SP_TRY(call)                                                                    \
+    do {                                                                                \
+        const cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                        \
+            rc = fail(c, UST_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            goto done;                                                                  \
+        }                                                                               \
+    } while (0)
+    {
+        SP_TRY(cudaMemsetAsync(d_lb, 0, (size_t)n * 4, c->stream));
+        SP_TRY(cudaMemsetAsync(d_words, 0, 4 * sizeof(unsigned long long), c->stream));
+        int s = start;
+        if (s < 0) {
+            max_degree_kernel<<<blocks, threads, 0, c->stream>>>(n, d_rp, d_words);
+            SP_TRY(cudaGetLastError());
+            SP_TRY(cudaMemcpyAsync(&key, d_words, sizeof(key), cudaMemcpyDeviceToHost, c->stream));
+            SP_TRY(cudaStreamSynchronize(c->stream));
+            s = 0x7FFFFFFF - (int)(uint32_t)(key & 0xFFFFFFFFull);
+        }
+        for (int sweep = 0; sweep < sweeps; ++sweep) {
+            bfs_init_kernel<<<blocks, threads, 0, c->stream>>>(n, s, d_dist, d_bpar);
+            for (int level = 0;; ++level) {
+                if (level > n) {
+                    rc = fail(c, UST_ETIMEOUT, "BFS did not terminate");
+                    goto done;
+                }
+                SP_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int32_t), c->stream));
+                bfs_pull_kernel<<<blocks, threads, 0, c->stream>>>(n, level, d_rp, d_ci, d_dist, d_bpar, d_flag);
+                SP_TRY(cudaGetLastError());
+                SP_TRY(cudaMemcpyAsync(&h_flag, d_flag, sizeof(h_flag), cudaMemcpyDeviceToHost, c->stream));
+                SP_TRY(cudaStreamSynchronize(c->stream));
+                if (h_flag == 0) break;
+            }
+            SP_TRY(cudaMemsetAsync(d_words, 0, sizeof(unsigned long long), c->stream));
+            sweep_update_kernel<<<blocks, threads, 0, c->stream>>>(n, d_dist, d_lb, d_words, d_bad);
+            SP_TRY(cudaGetLastError());
+            int bad = 0;
+            SP_TRY(cudaMemcpyAsync(&key, d_words, sizeof(key), cudaMemcpyDeviceToHost, c->stream));
+            SP_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+            SP_TRY(cudaStreamSynchronize(c->stream));
+            if (bad) {
+                rc = fail(c, UST_ENOTCONNECTED, "graph is not connected");
+                goto done;
+            }
+            s = 0x7FFFFFFF - (int)(uint32_t)(key & 0xFFFFFFFFull);  // the next source: the farthest vertex
+        }
+        SP_TRY(cudaMemsetAsync(d_words, 0xFF, sizeof(unsigned long long), c->stream));
+        min_bound_kernel<<<blocks, threads, 0, c->stream>>>(n, d_lb, d_words);
+        SP_TRY(cudaGetLastError());
+        SP_TRY(cudaMemcpyAsync(&key, d_words, sizeof(key), cudaMemcpyDeviceToHost, c->stream));
+        SP_TRY(cudaStreamSynchronize(c->stream));
+        *pivot = (int32_t)(uint32_t)(key & 0xFFFFFFFFull);
+        *bound = (int32_t)(key >> 32);
+    }
+#undef SP_TRY
+done:
+    release();
+    return rc;
+}
 
 int check_graph(Ctx *c, int n, int nnz, const int32_t *d_rp, const int32_t *d_ci, int *d_bad)
 {

@@ -215,6 +215,10 @@ inline void phase_close(Ctx *c, int ph)
 int run_bfs(Ctx *c);
 // The input checks of ust_init on a device CSR; d_bad: one int of scratch.
 int check_graph(Ctx *c, int n, int nnz, const int32_t *d_rp, const int32_t *d_ci, int *d_bad);
+// Pivot by eccentricity lower bounds from `sweeps` double-sweep BFS runs
+// (start < 0: the max-degree vertex); returns the vertex of least bound.
+int select_pivot(Ctx *c, int n, const int32_t *d_rp, const int32_t *d_ci, int sweeps, int start, int32_t *pivot,
+                 int32_t *bound);
 // Chooses the single-graph launch shape (requested or automatic) and sizes
 // the workspace for it.
 int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm);

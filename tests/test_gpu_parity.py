@@ -369,3 +369,19 @@ def test_edge_counts_bit_exact(pkg, orc, name, trees):
                     h2.close()
             h.reset(u)
             assert not h.edge_counts().any()
+
+
+@pytest.mark.parametrize("name", ["grid48", "rmat12", "ba3000", "er2000", "path50"])
+def test_select_pivot_equals_oracle(pkg, orc, name):
+    """ust_select_pivot: the same pivot and eccentricity bound as the oracle's
+    double sweeps (integer results, equal exactly)."""
+    g, _ = GRAPHS[name]()
+    for sweeps, start in ((10, -1), (3, 0)):
+        assert pkg.select_pivot(g.row_ptr, g.col_idx, sweeps, start) == orc.select_pivot(g, sweeps, start)
+
+
+def test_select_pivot_rejects_disconnected(pkg):
+    g = synth.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], lcc=False)
+    with pytest.raises(pkg.UstError) as e:
+        pkg.select_pivot(g.row_ptr, g.col_idx)
+    assert e.value.code == pkg.UST_ENOTCONNECTED

@@ -455,3 +455,36 @@ def test_sampled_edge_frequencies_match_resistances():
             assert c == T  # a bridge is in every spanning tree
         sigma = math.sqrt(max(r * (1 - r), 1e-12) / T)
         assert abs(f - r) <= 5 * sigma + 1e-12, (a, b, f, r)
+
+
+# ---------------------------------------------------------------- pivot selection
+
+def _exact_ecc(g):
+    A = csr_matrix((np.ones(g.nnz), g.col_idx, g.row_ptr), shape=(g.n, g.n))
+    return shortest_path(A, unweighted=True).max(axis=1).astype(np.int64)
+
+
+def test_double_sweep_bounds_are_lower_bounds_and_exact_on_trees():
+    import oracle
+    for g in small_graphs() + [synth.grid(9, 7), synth.rmat(8, 4, seed=3)]:
+        ecc = _exact_ecc(g)
+        piv, bound = oracle.select_pivot(g, sweeps=10)
+        assert bound <= ecc[piv]                        # a lower bound
+        assert bound <= ecc.min()                       # the least bound never exceeds the radius
+    rng = np.random.default_rng(5)
+    for n in (9, 17, 40):
+        parent = [int(rng.integers(0, v)) for v in range(1, n)]  # a random tree
+        t = synth.from_edges(n, list(range(1, n)), parent, name=f"tree{n}")
+        ecc = _exact_ecc(t)
+        piv, bound = oracle.select_pivot(t, sweeps=3)
+        # on a tree the second and third sources are the two ends of a diameter,
+        # and ecc(x) = max(dist(x, a), dist(x, b)) for those ends: the bound is exact
+        assert bound == ecc[piv] == ecc.min()
+    piv, bound = oracle.select_pivot(synth.path(21), sweeps=2)
+    assert (piv, bound) == (10, 10)
+    # 9x9 grid: the sweeps alternate between opposite corners, so the bound of
+    # the centre (8, the radius) is shared by other vertices; it is a bound,
+    # not the eccentricity, and the least bound equals the radius here
+    g = synth.grid(9, 9)
+    piv, bound = oracle.select_pivot(g, sweeps=10)
+    assert bound == 8 and _exact_ecc(g)[piv] >= 8
