@@ -89,10 +89,13 @@ typedef struct {
     double cg_tol;          /* relative residual ||b - L x|| / ||b|| of the column [1e-9] */
     int32_t max_pop_rounds; /* bound on cycle-popping rounds per tree [16 (2m ecc(u) + n) + 1024] */
     int32_t max_cg_iters;   /* bound on inner FP32 PCG iterations per refinement step [20000] */
-    int32_t skip_validation; /* 1: trust the CSR; 0: check order, loops, symmetry on the host [0] */
+    int32_t skip_validation; /* 1: trust the CSR; 0: check it on the device: row pointers, column
+                                range, self-loops, sorted rows, symmetry, isolated vertices [0] */
     int32_t graph_id;       /* fourth Philox counter word [0] */
-    int32_t block_threads;  /* threads per sampling CTA, 0 = tuned default */
-    int32_t ctas_per_sm;    /* sampling CTAs per SM, 0 = tuned default */
+    int32_t block_threads;  /* threads per sampling CTA: 64, 128, 256, 512 or 1024 (the global-memory
+                               sampler of graphs above 57,344 vertices: 256 or more) [0 = by graph size] */
+    int32_t ctas_per_sm;    /* sampling CTAs per SM, capped by what registers and shared memory allow
+                               [0 = as many as fit] */
     int32_t solve_fp64;     /* 1: run the whole column solve in FP64 (reference form) [0 = FP32 PCG
                                inside FP64 refinement] */
     void *stream;           /* cudaStream_t to issue work on [NULL = legacy default stream] */
@@ -136,11 +139,13 @@ typedef struct {
 /* Fills *o with the defaults. */
 UST_API void ust_default_opts(ust_opts *o);
 
-/* Creates a context for graph g and pivot u = pivot: validates (unless
- * skip_validation),
- * copies the CSR to the device, computes B_u, ecc(u) and f^c(u).
- * Errors: UST_EINVAL (bad CSR or pivot), UST_ENOTCONNECTED, UST_ENOMEM,
- * UST_ECUDA. On error *out is NULL. */
+/* Creates a context for graph g and pivot u = pivot: copies the CSR to the
+ * device, checks it there (unless skip_validation; see ust_csr), computes
+ * B_u, ecc(u), f^c(u) and the flattened BFS paths (Section 3.2, Algorithm 1)
+ * and sizes the sampler and solver scratch. Errors: UST_EINVAL (bad CSR or
+ * pivot), UST_ENOTCONNECTED (an isolated vertex or a vertex B_u does not
+ * reach), UST_ENOMEM, UST_ECUDA. On error *out is NULL and
+ * ust_last_error(NULL) describes the failure. */
 UST_API int ust_init(const ust_csr *g, int32_t pivot, const ust_opts *o, ust_ctx **out);
 
 /* A pivot of low eccentricity (Appendix D, choice of u; Theorem 1's running
