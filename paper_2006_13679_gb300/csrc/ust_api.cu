@@ -69,9 +69,10 @@ void release(Ctx *c)
 
 namespace ust {
 
-// Host checks of the CSR contract: row_ptr monotone from 0 to nnz, columns
-// in range and strictly increasing per row, no self-loops, every arc present
-// in both directions, no isolated vertex.
+// Batch contexts (ust_batch.cu). The CSR contract (row_ptr monotone from 0
+// to nnz, columns in range and strictly increasing per row, no self-loops,
+// every arc present in both directions, no isolated vertex) is checked on the
+// device by check_graph, for single graphs and for every graph of a batch.
 int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, const ust_opts &op);
 int batch_sample_aggregate(Ctx *c, int64_t n_trees, uint64_t seed);
 int64_t batch_tau(const Ctx *c, double eps);
