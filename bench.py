@@ -50,6 +50,9 @@ WORKLOADS = {
 }
 BATCH_GRAPHS = 256
 BATCH_TREES = 1024
+# Upper vertex counts of the library's batch size classes (kClassMaxN in
+# csrc/ust_common.cuh); --per-class times each class as a batch of its own.
+BATCH_CLASS_MAX_N = (4096, 8192, 14336, 28672, 56 * 1024, 2 ** 31 - 1)
 # CPU baseline sample of the batch workload: the first graphs, this many trees each
 BATCH_CPU_GRAPHS = 16
 BATCH_CPU_TREES = 64
@@ -344,6 +347,33 @@ def run_batch_gpu(args, rank: int, world: int, local_rank: int, dist) -> None:
                       "ms_per_step": loop_ms, "value": trees_step / (loop_ms / 1e3), "unit": "trees/s",
                       "batched_speedup": loop_ms / ms, "counts_equal_to_batch": same}
 
+    # each size class on its own (outside the timed region): where the
+    # sampler time of the batch goes
+    per_class = None
+    if args.per_class:
+        per_class = []
+        lo = 0
+        for hi in BATCH_CLASS_MAX_N:
+            idx = [i for i, g in enumerate(gs) if lo < g.n <= hi]
+            lo = hi
+            if not idx:
+                continue
+            with pkg.USTBatch([(gs[i].row_ptr, gs[i].col_idx) for i in idx], [pivots[i] for i in idx],
+                              stream=stream, skip_validation=True) as sb:
+                times = []
+                for k in range(3):  # the first run warms up
+                    sb.reset()
+                    sb.sample_aggregate(T, seed)
+                    torch.cuda.synchronize()
+                    if k > 0:
+                        times.append(sb.info()["sample_ms"])
+                shape = sb.graph_info(0)
+                per_class.append({"max_n": hi, "graphs": len(idx), "vertices": sum(gs[i].n for i in idx),
+                                  "arcs": sum(gs[i].nnz for i in idx), "trees": len(idx) * T,
+                                  "sample_ms": statistics.mean(times),
+                                  "draws_per_tree": sb.info()["last_draws"] / (len(idx) * T),
+                                  "sampler": f"{shape['sample_ctas']} CTAs x {shape['sample_threads']} threads"})
+
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -384,6 +414,8 @@ def run_batch_gpu(args, rank: int, world: int, local_rank: int, dist) -> None:
                 "cg_relres": info["cg_relres"], "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps, "e2e": e2e, "cpu_baseline": cpu,
                 "comparator": comparator}
+        if per_class is not None:
+            line["per_class"] = per_class
         print(json.dumps(line), flush=True)
     b.close()
     if dist is not None:
@@ -415,6 +447,8 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat16", choices=sorted(WORKLOADS))
+    ap.add_argument("--per-class", action="store_true",
+                    help="batch256: also time each size class of the batch on its own")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip the one-tree-per-launch + all-FP64-solve comparison")
     args = ap.parse_args()
