@@ -52,7 +52,7 @@ BATCH_GRAPHS = 256
 BATCH_TREES = 1024
 # Upper vertex counts of the library's batch size classes (kClassMaxN in
 # csrc/ust_common.cuh); --per-class times each class as a batch of its own.
-BATCH_CLASS_MAX_N = (4096, 8192, 14336, 28672, 56 * 1024, 2 ** 31 - 1)
+BATCH_CLASS_MAX_N = (4096, 8192, 14336, 28672, 56 * 1024, 0xFFFF, 2 ** 31 - 1)
 # CPU baseline sample of the batch workload: the first graphs, this many trees each
 BATCH_CPU_GRAPHS = 16
 BATCH_CPU_TREES = 64

@@ -46,6 +46,10 @@ struct GraphDesc {
 // Graphs of at most this many vertices run the sampler with its per-tree
 // state in shared memory (4 bytes per vertex; ids below 2^16).
 constexpr int kSmemMaxVertices = 56 * 1024;
+// The same sampler serves graphs up to this size (16-bit vertex ids below
+// the 0xFFFF sentinel): the words beyond kSmemMaxVertices live in a small
+// per-CTA tail in global memory.
+constexpr int kTierMaxVertices = 0xFFFF;
 
 // One sampler launch shape: threads per CTA (64, 128, 256, 512 or 1024) and
 // the persistent CTAs of the launch (a multiple of the SM count).
@@ -70,8 +74,8 @@ struct SolveResult {
 };
 // Size classes of a batch: the graphs with at most kClassMaxN[k] vertices
 // (and more than the previous bound) share one sampler launch and shape.
-constexpr int kNumClasses = 6;
-constexpr int kClassMaxN[kNumClasses] = {4096, 8192, 14336, 28672, kSmemMaxVertices, 0x7FFFFFFF};
+constexpr int kNumClasses = 7;
+constexpr int kClassMaxN[kNumClasses] = {4096, 8192, 14336, 28672, kSmemMaxVertices, kTierMaxVertices, 0x7FFFFFFF};
 
 // Per-CTA scratch of the sampling kernel: `kWsArrays` int32 arrays of
 // `stride` entries each, laid out array-major inside one CTA slot (the last

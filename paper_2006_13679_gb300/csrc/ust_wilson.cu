@@ -783,9 +783,10 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
 }
 
 // ---------------------------------------------------------------------------
-// The same three phases for graphs of at most kSmemMaxN vertices (ids below
-// 2^16), with the hot per-tree state in shared memory (4 bytes per vertex,
-// one n-word array whose view changes per phase):
+// The same three phases for graphs of at most kTierMaxVertices vertices
+// (ids below 0xFFFF), with the hot per-tree state in shared memory (4 bytes
+// per vertex, one n-word array whose view changes per phase; above
+// kSmemMaxVertices vertices its last words sit in a global tail):
 //   peeling   16-bit remaining in-degree | 16-bit successor
 //   rounds    16-bit round mark          | 16-bit successor
 //   sizes     32-bit word: pending children << 16 | summed sizes
@@ -801,21 +802,64 @@ constexpr uint16_t kFinal16 = 0xFFFFu;
 constexpr int kMaxStamp15 = 0x7FFE;
 constexpr uint16_t kVisited16 = 0x8000u;
 
-__device__ __forceinline__ uint32_t half_add(uint32_t *words, int v, int delta)
+// Shared words of the sampler: kSmemWords 32-bit words per CTA.
+constexpr int kSmemWords = ((kSmemMaxVertices + 1) / 2) * 2;
+// Workspace array that holds the words beyond kSmemWords (graphs between
+// kSmemMaxVertices and kTierMaxVertices vertices): at most
+// kTierMaxVertices + 1 - kSmemWords words, below one array's stride.
+constexpr int kTailArray = 9;
+static_assert(kTailArray < kWsArrays, "the tail is one of the CTA's workspace arrays");
+static_assert(kTierMaxVertices + 1 - kSmemWords <= kSmemMaxVertices,
+              "the tail fits one workspace array (stride >= max_n + 2 > kSmemMaxVertices)");
+static_assert(kTierMaxVertices < 0xFFFF + 1, "16-bit vertex ids stay below the 0xFFFF sentinel");
+
+// The per-tree words of the shared-memory sampler. Word i lives in shared
+// memory below kSmemWords; with kTier the words from kSmemWords on live in
+// the CTA's global tail. 16-bit element i is half (i & 1) of word i >> 1.
+template <bool kTier>
+struct TreeWords {
+    uint32_t *s;  // shared words
+    uint32_t *g;  // tail: word kSmemWords + j at g[j]
+    __device__ __forceinline__ uint32_t *word(int i) const
+    {
+        if constexpr (kTier) return i < kSmemWords ? s + i : g + (i - kSmemWords);
+        return s + i;
+    }
+    __device__ __forceinline__ uint16_t *half(int i) const
+    {
+        if constexpr (kTier)
+            return i < 2 * kSmemWords ? reinterpret_cast<uint16_t *>(s) + i
+                                      : reinterpret_cast<uint16_t *>(g) + (i - 2 * kSmemWords);
+        return reinterpret_cast<uint16_t *>(s) + i;
+    }
+};
+// Array views into the tree words, starting at word (or half) `base`.
+template <bool kTier>
+struct Words32 {
+    TreeWords<kTier> t;
+    int base;
+    __device__ __forceinline__ uint32_t &operator[](int i) const { return *t.word(base + i); }
+};
+template <bool kTier>
+struct Halves16 {
+    TreeWords<kTier> t;
+    int base;
+    __device__ __forceinline__ uint16_t &operator[](int i) const { return *t.half(base + i); }
+};
+
+template <class Words>
+__device__ __forceinline__ uint32_t half_add(const Words &words, int v, int delta)
 {
     const int sh = (v & 1) << 4;
-    const uint32_t old = atomicAdd(words + (v >> 1), (uint32_t)delta << sh);
+    const uint32_t old = atomicAdd(&words[v >> 1], (uint32_t)delta << sh);
     return (old >> sh) & 0xFFFFu;
 }
 
-template <int BT>
+template <int BT, bool kTier>
 __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_kernel(SampleParams p)
 {
     extern __shared__ uint32_t s_dyn[];
     const int tid = threadIdx.x;
-    uint16_t *lo16 = reinterpret_cast<uint16_t *>(s_dyn);        // counts, then marks
-    uint32_t *lo32 = s_dyn;                                      // the same, as words
-    uint32_t *C = s_dyn;                                         // sizes / preorder words
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
     int32_t *nxt = base;              // the tree's parent array at the end
@@ -829,6 +873,10 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
     int32_t *off = XA;
     int32_t *Rp = p.Rp + (long long)blockIdx.x * p.max_n;
     constexpr uint32_t kC16 = 1u << 16;
+    const TreeWords<kTier> tw{s_dyn, reinterpret_cast<uint32_t *>(base + kTailArray * S_)};
+    const Halves16<kTier> lo16{tw, 0};  // counts, then marks
+    const Words32<kTier> lo32{tw, 0};   // the same, as words
+    const Words32<kTier> C{tw, 0};      // sizes / preorder words
 
     __shared__ long long s_tree;
     __shared__ int s_cnt, s_err, s_qn, s_qh, s_linked, s_mark_on, s_maxwalk;
@@ -857,7 +905,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
         const int n = gd.n, u = gd.u;
         const uint32_t tree = (uint32_t)t;
         const int nhalf = (n + 1) >> 1;                                // words of one 16-bit array
-        uint16_t *nx16 = reinterpret_cast<uint16_t *>(s_dyn + nhalf);  // successors
+        const Halves16<kTier> nx16{tw, 2 * nhalf};  // successors
         const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
         if (tid == 0) tmark = clock64();
 
@@ -1419,17 +1467,25 @@ size_t smem_bytes_for(int max_n) { return (size_t)((max_n + 1) / 2) * 2 * sizeof
 
 int64_t stride_for(int max_n) { return ((int64_t)max_n + 2 + 31) / 32 * 32; }
 
-// Graphs above kSmemMaxN run the global-memory kernel, built for 256 threads
-// and more; graphs within it run the shared-memory kernel at any shape.
+// Graphs of at most kSmemMaxN vertices run the shared-memory kernel at any
+// shape; up to kTierMaxVertices the same kernel with its last words in the
+// workspace tail; larger graphs the global-memory kernel, built for 256
+// threads and more.
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
     if (p.max_n <= kSmemMaxN) {
         const size_t bytes = smem_bytes_for(p.max_n);
-        cudaError_t e = cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT>,
+        cudaError_t e = cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
-        sample_aggregate_smem_kernel<BT><<<grid, BT, bytes, st>>>(p);
+        sample_aggregate_smem_kernel<BT, false><<<grid, BT, bytes, st>>>(p);
+    } else if (p.max_n <= kTierMaxVertices) {
+        const size_t bytes = (size_t)kSmemWords * sizeof(uint32_t);
+        cudaError_t e = cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        sample_aggregate_smem_kernel<BT, true><<<grid, BT, bytes, st>>>(p);
     } else {
         if constexpr (BT >= 256)
             sample_aggregate_kernel<BT, false><<<grid, BT, 0, st>>>(p);
@@ -1459,11 +1515,19 @@ int resident_ctas(int max_n)
     int blocks = 0;
     if (max_n <= kSmemMaxN) {
         const size_t bytes = smem_bytes_for(max_n);
-        if (cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)bytes) != cudaSuccess)
             return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_smem_kernel<BT>, BT, bytes) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_smem_kernel<BT, false>, BT,
+                                                          bytes) != cudaSuccess)
+            return 0;
+    } else if (max_n <= kTierMaxVertices) {
+        const size_t bytes = (size_t)kSmemWords * sizeof(uint32_t);
+        if (cudaFuncSetAttribute(sample_aggregate_smem_kernel<BT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_smem_kernel<BT, true>, BT,
+                                                          bytes) != cudaSuccess)
             return 0;
     } else {
         if constexpr (BT >= 256) {
@@ -1494,7 +1558,7 @@ int default_bt(int max_n)
     if (max_n <= 8192) return 128;
     if (max_n <= 14336) return 256;
     if (max_n <= 28672) return 512;
-    if (max_n <= kSmemMaxN) return 1024;
+    if (max_n <= kTierMaxVertices) return 1024;
     // above the shared-memory sampler: two trees per SM while the per-tree
     // arrays are small, one whole-SM tree per SM for the very large graphs
     return max_n <= 262144 ? 512 : 1024;
@@ -1505,7 +1569,7 @@ bool valid_bt(int bt) { return bt == 64 || bt == 128 || bt == 256 || bt == 512 |
 int choose_cfg(Ctx *c, int max_n, int req_bt, int req_cps, LaunchCfg *out)
 {
     int bt = valid_bt(req_bt) ? req_bt : default_bt(max_n);
-    if (max_n > kSmemMaxN && bt < 256) bt = 256;
+    if (max_n > kTierMaxVertices && bt < 256) bt = 256;
     const int resident = resident_ctas_for(bt, max_n);
     if (resident < 1) return fail(c, UST_EINVAL, "no sampler launch shape fits this graph at the requested threads");
     const int cps = req_cps > 0 ? std::min(req_cps, resident) : resident;

@@ -241,10 +241,10 @@ def test_repeat_runs_are_identical(pkg):
 
 @pytest.mark.parametrize("maker", [lambda: synth.ba(70000, 3, seed=9), lambda: synth.rmat(17, 8, seed=2)])
 def test_counts_above_shared_memory_limit(pkg, orc, maker):
-    """Graphs with more than 56k vertices keep their per-tree counters in
+    """Graphs with more than 65,535 vertices keep their per-tree counters in
     global memory instead of shared memory: R bit-exact as well."""
     g = maker()
-    assert g.n > 56 * 1024
+    assert g.n > 0xFFFF
     u = synth.max_degree_vertex(g)
     with make(pkg, g, u) as h:
         h.sample_aggregate(300, 21)
@@ -255,6 +255,31 @@ def test_counts_above_shared_memory_limit(pkg, orc, maker):
         nxt, pops = h.sample_trees(100, 3, 21, with_pops=True)
         for i in range(3):
             ref, ref_pops, _ = orc.wilson(g, u, 100 + i, 21)
+            assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
+
+
+@pytest.mark.parametrize("maker,bt", [
+    (lambda: synth.ba(57345, 3, seed=4), 0),     # the first tail word in use
+    (lambda: synth.er(60000, 10.0, seed=6), 0),
+    (lambda: synth.er(60000, 10.0, seed=6), 256),
+    (lambda: synth.ba(65535, 2, seed=8), 0),     # the largest graph with 16-bit ids
+])
+def test_counts_with_shared_words_in_a_global_tail(pkg, orc, maker, bt):
+    """Graphs between 56k and 65,535 vertices run the shared-memory sampler
+    with its last words in a per-CTA global tail: R, the draws and sampled
+    trees with their pop counts bit-exact."""
+    g = maker()
+    assert 56 * 1024 < g.n <= 0xFFFF
+    u = synth.max_degree_vertex(g)
+    with make(pkg, g, u, block_threads=bt) as h:
+        h.sample_aggregate(200, 23)
+        _, _, par = orc.bfs(g, u)
+        R_ref, steps = orc.sample_aggregate(g, u, par, 0, 200, 23, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert h.info()["draws"] == steps
+        nxt, pops = h.sample_trees(50, 3, 23, with_pops=True)
+        for i in range(3):
+            ref, ref_pops, _ = orc.wilson(g, u, 50 + i, 23)
             assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
 
 
