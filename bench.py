@@ -36,7 +36,7 @@ SEED = 0
 # DRAM bytes (read + write) of one sampler launch on the rmat16 workload, from the ncu capture
 # summarised in profiles/sample_aggregate_rmat16.md. Reported only while the kernel source is
 # the one the capture was taken on.
-TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "9eecf47baa2e9d62c4179beae41cb655c6eeec7f", "bytes": 1.989883e9 + 4.069013e9}
+TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "7ded4869447e46db18d7397ada845593f5700b75", "bytes": 1.990219e9 + 4.073855e9}
 
 # workload -> (description, oracle sample in trees for the CPU baseline; None = all)
 WORKLOADS = {
