@@ -42,3 +42,16 @@ def test_reference_arm_other_ranks_exit_without_work():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_per_class_bounds_match_the_library():
+    """bench.py --per-class groups the batch by the library's size classes."""
+    import re
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", "ust_common.cuh")).read()
+    consts = {m.group(1): m.group(2) for m in re.finditer(r"constexpr int (\w+) = ([^;]+);", src)}
+    body = re.search(r"kClassMaxN\[kNumClasses\] = \{([^}]*)\}", src).group(1)
+    bounds = tuple(int(eval(consts.get(t.strip(), t.strip()), {})) for t in body.split(","))
+    assert bounds == bench.BATCH_CLASS_MAX_N
+    assert len(bounds) == int(consts["kNumClasses"])
