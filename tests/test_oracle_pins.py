@@ -488,3 +488,55 @@ def test_double_sweep_bounds_are_lower_bounds_and_exact_on_trees():
     g = synth.grid(9, 9)
     piv, bound = oracle.select_pivot(g, sweeps=10)
     assert bound == 8 and _exact_ecc(g)[piv] >= 8
+
+
+# --------------------------------------------- biconnected-component variant
+
+def _parent_block_walk_graph(g, u, par, nx):
+    """The CSR in which v != u keeps only its neighbours in its parent block
+    (the block of the edge (v, bfs_parent(v))); u keeps its row (it never
+    draws)."""
+    G = nx.Graph()
+    G.add_edges_from(map(tuple, g.edges().tolist()))
+    block = {}
+    for b, es in enumerate(nx.biconnected_component_edges(G)):
+        for a, c in es:
+            block[(a, c)] = block[(c, a)] = b
+    rp, ci = [0], []
+    for v in range(g.n):
+        row = [int(w) for w in g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]]
+        if v != u:
+            pb = block[(v, int(par[v]))]
+            row = [w for w in row if block[(v, w)] == pb]
+        ci += row
+        rp.append(len(ci))
+    return synth.graphs.Graph(g.n, np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), name="walk")
+
+
+def test_parent_block_walks_sample_uniform_trees_toward_u(orc):
+    """Appendix D's biconnected-component variant in the form that was measured
+    (and not built): every vertex v != u walks only inside its parent block.
+    Every cycle lies in one block, so each block pops its cycles on its own and
+    yields a uniform tree of the block rooted at its vertex nearest u; their
+    union is uniform over the spanning trees of G and already oriented toward
+    u. Brute force: chi-square over all 36 spanning trees, and every sample a
+    tree of G rooted at u."""
+    nx = pytest.importorskip("networkx")
+    # triangle {0,1,2}, triangle {2,3,4}, square {4,5,6,7}, bridge {7,8}
+    src = [0, 1, 0, 2, 3, 2, 4, 5, 6, 4, 7]
+    dst = [1, 2, 2, 3, 4, 4, 5, 6, 7, 7, 8]
+    g = synth.from_edges(9, src, dst, lcc=False)
+    u = 5
+    _, _, par = orc.bfs(g, u)
+    w = _parent_block_walk_graph(g, u, par, nx)
+    assert w.nnz < g.nnz  # the cut vertices 2, 4 and 7 lose their other blocks
+    trees = orc.spanning_trees(g)
+    assert len(trees) == 3 * 3 * 4 * 1
+    index = {t: i for i, t in enumerate(trees)}
+    counts = np.zeros(len(trees), dtype=np.int64)
+    for t in range(400 * len(trees)):
+        nxt, _, _ = orc.cycle_pop(w, u, t, 99)
+        edges = orc.tree_edges_of(nxt)
+        assert np.array_equal(orc.root_tree(edges, g.n, u), nxt)
+        counts[index[edges]] += 1
+    assert stats.chisquare(counts).pvalue > 1e-4, counts
