@@ -233,15 +233,109 @@ def tree_arcs(g, nxt, u: int) -> np.ndarray:
     return out
 
 
-def edge_counts(g, u: int, t0: int, t1: int, seed: int, graph: int = 0) -> np.ndarray:
-    """Per CSR arc v -> w, the number of trees t0 .. t1-1 (Wilson's loop-erased
-    walks, Appendix A.2) in which w is v's parent: sampling USTs and counting
-    the trees each edge appears in (appendix on Kirchhoff edge centrality)."""
+def edge_counts(g, u: int, t0: int, t1: int, seed: int, graph: int = 0, walk=None) -> np.ndarray:
+    """Per CSR arc v -> w of g, the number of trees t0 .. t1-1 (Wilson's
+    loop-erased walks, Appendix A.2) in which w is v's parent: sampling USTs
+    and counting the trees each edge appears in (appendix on Kirchhoff edge
+    centrality). walk: the rows the walks draw from (parent_block_graph for
+    the biconnected-component variant), default g."""
     counts = np.zeros(g.nnz, dtype=np.int64)
     for t in range(t0, t1):
-        nxt, _, _ = wilson(g, u, t, seed, graph)
+        nxt, _, _ = wilson(g if walk is None else walk, u, t, seed, graph)
         np.add.at(counts, tree_arcs(g, nxt, u), 1)
     return counts
+
+
+# ------------------------------------------- biconnected-component variant
+
+class CSR:
+    """Rows of a (possibly directed) sampling graph: n, row_ptr, col_idx."""
+
+    def __init__(self, n: int, row_ptr: np.ndarray, col_idx: np.ndarray):
+        self.n = int(n)
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.shape[0])
+
+
+def blocks(g) -> np.ndarray:
+    """Block (biconnected component) id of every CSR arc of g; both arcs of an
+    edge get the same id. Hopcroft and Tarjan's depth-first search with an
+    edge stack: every tree or back edge is pushed once; when the search
+    leaves a tree edge (p, v) with low(v) >= disc(p), p separates v's subtree
+    and the edges above (p, v) on the stack, (p, v) included, form one
+    block. Appendix D samples the UST block by block (Hayashi et al.)."""
+    rp, ci = _csr(g)
+    n = g.n
+    disc = np.full(n, -1, dtype=np.int64)
+    low = np.zeros(n, dtype=np.int64)
+    arc_block = np.full(ci.shape[0], -1, dtype=np.int64)
+    clock, nb = 0, 0
+    estack = []
+    for s in range(n):
+        if disc[s] >= 0:
+            continue
+        disc[s] = low[s] = clock
+        clock += 1
+        frames = [[s, -1, int(rp[s]), -1]]  # vertex, parent, next arc, tree arc into the vertex
+        while frames:
+            fr = frames[-1]
+            v, p, it, tarc = fr
+            if it < rp[v + 1]:
+                fr[2] = it + 1
+                w = int(ci[it])
+                if disc[w] < 0:
+                    estack.append(it)
+                    disc[w] = low[w] = clock
+                    clock += 1
+                    frames.append([w, v, int(rp[w]), it])
+                elif w != p and disc[w] < disc[v]:  # back edge to an ancestor
+                    estack.append(it)
+                    low[v] = min(low[v], disc[w])
+            else:
+                frames.pop()
+                if p >= 0:
+                    low[p] = min(low[p], low[v])
+                    if low[v] >= disc[p]:
+                        while True:
+                            a = estack.pop()
+                            arc_block[a] = nb
+                            if a == tarc:
+                                break
+                        nb += 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp.astype(np.int64)))
+    for a in np.nonzero(arc_block < 0)[0]:  # the reverse arcs take their edge's block
+        v, w = int(src[a]), int(ci[a])
+        row = ci[rp[w]:rp[w + 1]]
+        arc_block[a] = arc_block[rp[w] + int(np.searchsorted(row, v))]
+    return arc_block
+
+
+def parent_block_graph(g, u: int, bfs_parent=None) -> CSR:
+    """Sampling rows of the biconnected-component variant (Appendix D): every
+    v != u keeps, in CSR order, its neighbours inside its parent block, the
+    block of the edge (v, bfs_parent(v)); u's row is empty (the root never
+    draws). Every cycle lies in one block, so Wilson on these rows samples
+    each block's tree on its own, rooted at the block's vertex nearest u, and
+    the union is a uniform spanning tree of g directed toward u."""
+    rp, ci = _csr(g)
+    if bfs_parent is None:
+        _, _, bfs_parent = bfs(g, u)
+    ab = blocks(g)
+    deg = np.diff(rp.astype(np.int64))
+    pb = np.full(g.n, -2, dtype=np.int64)
+    for v in range(g.n):
+        if v == u:
+            continue
+        row = ci[rp[v]:rp[v + 1]]
+        pb[v] = ab[rp[v] + int(np.searchsorted(row, bfs_parent[v]))]
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    keep = ab == pb[src]
+    row_ptr = np.concatenate([[0], np.cumsum(np.bincount(src[keep], minlength=g.n))])
+    return CSR(g.n, row_ptr, ci[keep])
 
 
 def centralities(diag) -> dict:

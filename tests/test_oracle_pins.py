@@ -492,25 +492,53 @@ def test_double_sweep_bounds_are_lower_bounds_and_exact_on_trees():
 
 # --------------------------------------------- biconnected-component variant
 
-def _parent_block_walk_graph(g, u, par, nx):
-    """The CSR in which v != u keeps only its neighbours in its parent block
-    (the block of the edge (v, bfs_parent(v))); u keeps its row (it never
-    draws)."""
-    G = nx.Graph()
-    G.add_edges_from(map(tuple, g.edges().tolist()))
-    block = {}
-    for b, es in enumerate(nx.biconnected_component_edges(G)):
-        for a, c in es:
-            block[(a, c)] = block[(c, a)] = b
-    rp, ci = [0], []
-    for v in range(g.n):
-        row = [int(w) for w in g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]]
-        if v != u:
-            pb = block[(v, int(par[v]))]
-            row = [w for w in row if block[(v, w)] == pb]
-        ci += row
-        rp.append(len(ci))
-    return synth.graphs.Graph(g.n, np.array(rp, dtype=np.int32), np.array(ci, dtype=np.int32), name="walk")
+def _block_example():
+    """Triangle {0,1,2}, triangle {2,3,4}, square {4,5,6,7}, bridge {7,8}:
+    cut vertices 2, 4 and 7, 3 * 3 * 4 * 1 = 36 spanning trees."""
+    src = [0, 1, 0, 2, 3, 2, 4, 5, 6, 4, 7]
+    dst = [1, 2, 2, 3, 4, 4, 5, 6, 7, 7, 8]
+    return synth.from_edges(9, src, dst, lcc=False)
+
+
+def _same_partition(a, b) -> bool:
+    m1, m2 = {}, {}
+    for x, y in zip(a, b):
+        if m1.setdefault(x, y) != y or m2.setdefault(y, x) != x:
+            return False
+    return True
+
+
+def test_blocks_textbook_cases(orc):
+    """Every edge of a tree is a bridge (its own block); a cycle, a grid and a
+    complete graph are one block; the example has its four blocks."""
+    for g, nb in [(synth.path(7), 6), (synth.star(6), 5), (synth.ba(60, 1, seed=3), 59), (synth.cycle(9), 1),
+                  (synth.grid(5, 4), 1), (synth.complete(6), 1)]:
+        ab = orc.blocks(g)
+        assert len(set(ab.tolist())) == nb
+        src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        rev = {(int(a), int(b)): int(x) for a, b, x in zip(src, g.col_idx, ab)}
+        assert all(rev[(b, a)] == x for (a, b), x in rev.items())  # both arcs of an edge agree
+    ab = orc.blocks(_block_example())
+    sizes = sorted(np.bincount(ab).tolist())
+    assert sizes == [2, 6, 6, 8]  # arcs per block: bridge, two triangles, square
+
+
+def test_blocks_match_networkx(orc):
+    """The oracle's Hopcroft-Tarjan blocks equal networkx's biconnected
+    components (an independent implementation) on sparse random graphs."""
+    nx = pytest.importorskip("networkx")
+    graphs = [synth.er(400, 2.2, seed=s) for s in range(4)] + [synth.ba(300, 2, seed=5), synth.rmat(10, 4, seed=3),
+                                                               _block_example()]
+    for g in graphs:
+        G = nx.Graph()
+        G.add_edges_from(map(tuple, g.edges().tolist()))
+        ref = {}
+        for b, es in enumerate(nx.biconnected_component_edges(G)):
+            for a, c in es:
+                ref[(a, c)] = ref[(c, a)] = b
+        src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        want = [ref[(int(a), int(c))] for a, c in zip(src, g.col_idx)]
+        assert _same_partition(orc.blocks(g).tolist(), want)
 
 
 def test_parent_block_walks_sample_uniform_trees_toward_u(orc):
@@ -521,15 +549,11 @@ def test_parent_block_walks_sample_uniform_trees_toward_u(orc):
     union is uniform over the spanning trees of G and already oriented toward
     u. Brute force: chi-square over all 36 spanning trees, and every sample a
     tree of G rooted at u."""
-    nx = pytest.importorskip("networkx")
-    # triangle {0,1,2}, triangle {2,3,4}, square {4,5,6,7}, bridge {7,8}
-    src = [0, 1, 0, 2, 3, 2, 4, 5, 6, 4, 7]
-    dst = [1, 2, 2, 3, 4, 4, 5, 6, 7, 7, 8]
-    g = synth.from_edges(9, src, dst, lcc=False)
+    g = _block_example()
     u = 5
-    _, _, par = orc.bfs(g, u)
-    w = _parent_block_walk_graph(g, u, par, nx)
+    w = orc.parent_block_graph(g, u)
     assert w.nnz < g.nnz  # the cut vertices 2, 4 and 7 lose their other blocks
+    assert w.row_ptr[u + 1] == w.row_ptr[u]  # the root draws nothing
     trees = orc.spanning_trees(g)
     assert len(trees) == 3 * 3 * 4 * 1
     index = {t: i for i, t in enumerate(trees)}
