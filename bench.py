@@ -422,18 +422,21 @@ def run_batch_gpu(args, rank: int, world: int, local_rank: int, dist) -> None:
         dist.destroy_process_group()
 
 
-def cpu_baseline(g, u, T, sample) -> dict:
+def cpu_baseline(g, u, T, sample, wilson_blocks: bool = False) -> dict:
     import oracle
     threads = oracle.max_threads()
     ecc, dist, par = oracle.bfs(g, u)
-    oracle.sample_aggregate(g, u, par, 0, min(16, sample), SEED, threads=threads)  # warm
+    walk = oracle.parent_block_graph(g, u, par) if wilson_blocks else g  # rows built before the timed step
+    oracle.sample_aggregate(walk, u, par, 0, min(16, sample), SEED, threads=threads)  # warm
     t0 = time.perf_counter()
     ecc, dist, par = oracle.bfs(g, u)
-    R, _ = oracle.sample_aggregate(g, u, par, 0, sample, SEED, threads=threads)
+    R, _ = oracle.sample_aggregate(walk, u, par, 0, sample, SEED, threads=threads)
     x, _, _, _ = oracle.cg(g, u, tol=1e-9)
     oracle.combine(R, sample, x, u)
     sec = time.perf_counter() - t0
     what = "one full step" if sample == T else f"BFS + {sample} of the {T} trees"
+    if wilson_blocks:
+        what += " on the parent-block rows (built outside the timed step)"
     return {"value": sample / sec, "unit": "trees/s", "cores": threads, "kind": "oracle",
             "sample": f"{what} + FP64 CG + combine, OpenMP over trees", "seconds": sec}
 
@@ -447,6 +450,9 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="rmat16", choices=sorted(WORKLOADS))
+    ap.add_argument("--wilson-blocks", action="store_true",
+                    help="single-graph workloads: walks inside each vertex's parent block "
+                         "(the biconnected-component variant)")
     ap.add_argument("--per-class", action="store_true",
                     help="batch256: also time each size class of the batch on its own")
     ap.add_argument("--no-comparator", action="store_true",
@@ -476,6 +482,8 @@ def main() -> None:
     pkg.build()
     from paper_2006_13679_gb300 import parallel
     if args.workload == "batch256":
+        if args.wilson_blocks:
+            raise SystemExit("--wilson-blocks applies to the single-graph workloads")
         run_batch_gpu(args, rank, world, local_rank, dist)
         return
     g, u, T0, eps = synth.workload(args.workload)
@@ -484,7 +492,7 @@ def main() -> None:
     stream = torch.cuda.Stream()
     rp_d = torch.from_numpy(g.row_ptr).cuda()
     ci_d = torch.from_numpy(g.col_idx).cuda()
-    h = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True)
+    h = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, wilson_blocks=args.wilson_blocks)
     diag_d = torch.empty(g.n, dtype=torch.float64, device="cuda")
     counts_d = torch.empty(g.n, dtype=torch.int64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -543,7 +551,7 @@ def main() -> None:
     try:
         import hashlib
         src = os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", "ust_wilson.cu")
-        if (args.workload == TRAFFIC_CAPTURE["workload"]
+        if (args.workload == TRAFFIC_CAPTURE["workload"] and not args.wilson_blocks
                 and hashlib.sha1(open(src, "rb").read()).hexdigest() == TRAFFIC_CAPTURE["sha1"]):
             traffic = TRAFFIC_CAPTURE["bytes"]
     except OSError:
@@ -557,7 +565,7 @@ def main() -> None:
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with pkg.UST(g.row_ptr, g.col_idx, u) as he:
+        with pkg.UST(g.row_ptr, g.col_idx, u, wilson_blocks=args.wilson_blocks) as he:
             he.sample_aggregate(T, seed)
             d_host = he.diag()
         t1 = time.perf_counter()
@@ -573,7 +581,8 @@ def main() -> None:
     # once, on the same stream and events, outside the measured steps.
     comparator = None
     if not args.no_comparator and T <= 8192:
-        hc = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, solve_fp64=True)
+        hc = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, solve_fp64=True,
+                     wilson_blocks=args.wilson_blocks)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -595,14 +604,17 @@ def main() -> None:
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(g, u, T, min(T, WORKLOADS[args.workload][1] or T))
+            cpu = cpu_baseline(g, u, T, min(T, WORKLOADS[args.workload][1] or T), args.wilson_blocks)
         line = {"metric": METRIC, "value": value, "unit": "trees/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][0]}; n={g.n} m={g.m}, "
                                        f"pivot {u}, {T} trees per GPU (tree ids rank*{T} onwards), seed {SEED}",
                            "l2": "flushed between timed steps (256 MB write)",
-                           "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads"},
+                           "sampler": f"{info['sample_ctas']} CTAs x {info['sample_threads']} threads",
+                           "walks": ("inside each vertex's parent block (biconnected-component variant; "
+                                     "the step's reset rebuilds the rows)" if args.wilson_blocks
+                                     else "plain Wilson rooted at the pivot")},
                 "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,
                                             "solve": statistics.mean(solve_ms)},
                 "sampler_cycles_per_tree": dict(zip(["first_draws", "in_degrees", "leaf_queue", "peeling",

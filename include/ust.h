@@ -98,6 +98,16 @@ typedef struct {
                                [0 = as many as fit] */
     int32_t solve_fp64;     /* 1: run the whole column solve in FP64 (reference form) [0 = FP32 PCG
                                inside FP64 refinement] */
+    int32_t wilson_blocks;  /* 1: the biconnected-component variant of Wilson's algorithm (Appendix D,
+                               after Hayashi et al.): every v != u draws its stack entries only among
+                               its neighbours in its parent block, the block of the edge
+                               (v, bfs_parent(v)), in CSR order. Each block then samples its own
+                               uniform tree rooted at its vertex nearest u; the union is a uniform
+                               spanning tree directed toward u, so R keeps its meaning, but for the
+                               same seed the trees differ from plain Wilson's. The rows are rebuilt
+                               with B_u (ust_init, ust_reset); arc counts stay per input arc.
+                               Single-graph contexts only (ust_init_batch: UST_EINVAL)
+                               [0 = plain Wilson rooted at u] */
     void *stream;           /* cudaStream_t to issue work on [NULL = legacy default stream] */
 } ust_opts;
 
@@ -188,8 +198,11 @@ UST_API int ust_batch_graph_info(const ust_ctx *c, int32_t g, ust_info *out);
 
 /* Re-targets the context to pivot u = pivot on the same graph: recomputes
  * B_u, ecc(u) and f^c(u) and clears R, the tree count and the cached column
- * (Algorithm 1 from its first line). No allocation. A batch context keeps
- * its pivots: pivot must be -1 there. Errors: UST_EINVAL, UST_ECUDA. */
+ * (Algorithm 1 from its first line). No allocation, except with
+ * wilson_blocks: the walk rows are rebuilt for the new B_u with 24 bytes per
+ * vertex of temporary device memory. A batch context keeps its pivots:
+ * pivot must be -1 there. Errors: UST_EINVAL, UST_ENOMEM (wilson_blocks),
+ * UST_ECUDA. */
 UST_API int ust_reset(ust_ctx *c, int32_t pivot);
 
 /* Samples trees with ids [trees, trees + n_trees) under `seed` and adds their

@@ -34,6 +34,9 @@ void release(Ctx *c)
     cudaFree(c->d_flag);
     cudaFree(c->d_pathptr);
     cudaFree(c->d_path);
+    cudaFree(c->d_wrp);
+    cudaFree(c->d_wci);
+    cudaFree(c->d_wmap);
     cudaFree(c->d_ws);
     cudaFree(c->d_Rp);
     cudaFree(c->d_R);
@@ -139,6 +142,11 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     }
     int rc = ust::run_bfs(c);
     if (rc) return rc;
+    if (op.wilson_blocks) {
+        c->blocks = true;
+        rc = ust::build_block_rows(c);
+        if (rc) return rc;
+    }
     rc = ust::alloc_sampler(c, op.block_threads, op.ctas_per_sm);
     if (rc) return rc;
     rc = ust::alloc_solver(c);
@@ -146,6 +154,29 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return UST_OK;
 }
+
+// The sampler draws from the context's CSR pointers. With the
+// biconnected-component variant they name the walk rows (each vertex's
+// neighbours in its parent block) for the length of one sampler call; B_u,
+// the checks and the solve keep using the input graph.
+struct SamplingRows {
+    Ctx *c;
+    int32_t *rp, *ci;
+    explicit SamplingRows(Ctx *ctx) : c(ctx), rp(ctx->d_rp), ci(ctx->d_ci)
+    {
+        if (c->blocks) {
+            c->d_rp = c->d_wrp;
+            c->d_ci = c->d_wci;
+        }
+    }
+    ~SamplingRows()
+    {
+        c->d_rp = rp;
+        c->d_ci = ci;
+    }
+    SamplingRows(const SamplingRows &) = delete;
+    SamplingRows &operator=(const SamplingRows &) = delete;
+};
 
 int copy_out(Ctx *c, void *dst, const void *src, size_t bytes, int32_t on_device)
 {
@@ -195,6 +226,10 @@ int ust_init_batch(const ust_csr *gs, const int32_t *pivots, int32_t count, cons
     *out = nullptr;
     if (!gs || !pivots || count < 1) {
         g_init_error = "invalid batch (need count >= 1 graphs and pivots)";
+        return UST_EINVAL;
+    }
+    if (o && o->wilson_blocks) {
+        g_init_error = "wilson_blocks applies to single-graph contexts";
         return UST_EINVAL;
     }
     ust_ctx *h = new (std::nothrow) ust_ctx;
@@ -307,7 +342,9 @@ int ust_reset(ust_ctx *h, int32_t pivot)
     c->x_valid = false;
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * 8, c->stream));
     if (c->d_ecount) UST_CUDA_TRY(cudaMemsetAsync(c->d_ecount, 0, (size_t)c->nnz * 8, c->stream));
-    return ust::run_bfs(c);
+    const int rc = ust::run_bfs(c);
+    if (rc || !c->blocks) return rc;
+    return ust::build_block_rows(c);  // parent blocks follow the new B_u
 }
 
 int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
@@ -323,8 +360,12 @@ int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
                                      c->stream));
     int64_t draws = 0, rounds = 0;
     int max_rounds = 0, max_depth = 0;
-    const int rc = ust::run_sampler(c, c->trees, c->trees + n_trees, seed, c->d_Rtmp, nullptr, nullptr, &draws,
-                                    &rounds, &max_rounds, &max_depth);
+    int rc;
+    {
+        SamplingRows rows(c);
+        rc = ust::run_sampler(c, c->trees, c->trees + n_trees, seed, c->d_Rtmp, nullptr, nullptr, &draws, &rounds,
+                              &max_rounds, &max_depth);
+    }
     if (rc) return rc;
     std::swap(c->d_R, c->d_Rtmp);
     std::swap(c->d_ecount, c->d_ecount_tmp);
@@ -427,6 +468,12 @@ int ust_get_edge_counts(ust_ctx *h, int64_t *counts_out, int32_t out_on_device)
     if (!h) return UST_EINVAL;
     Ctx *c = &h->c;
     if (!c->d_ecount) return ust::fail(c, UST_ESTATE, "arc counting is off (ust_track_edges)");
+    if (!counts_out) return ust::fail(c, UST_EINVAL, "null output pointer");
+    if (c->blocks) {  // counts of walk-row entries, moved to the input CSR's arcs
+        const int rc = ust::scatter_block_counts(c, c->d_ecount, c->d_ecount_tmp);
+        if (rc) return rc;
+        return copy_out(c, counts_out, c->d_ecount_tmp, (size_t)c->nnz * sizeof(int64_t), out_on_device);
+    }
     return copy_out(c, counts_out, c->d_ecount, (size_t)c->nnz * sizeof(int64_t), out_on_device);
 }
 
@@ -466,7 +513,11 @@ int ust_tree_range_counts(ust_ctx *h, int64_t t0, int64_t t1, uint64_t seed, int
     if (!R_out || t0 < 0 || t1 < t0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
     if (c->batch) return ust::fail(c, UST_EINVAL, "ust_tree_range_counts applies to single-graph contexts");
     UST_CUDA_TRY(cudaMemsetAsync(c->d_Rtmp, 0, (size_t)c->n * 8, c->stream));
-    const int rc = ust::run_sampler(c, t0, t1, seed, c->d_Rtmp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    int rc;
+    {
+        SamplingRows rows(c);
+        rc = ust::run_sampler(c, t0, t1, seed, c->d_Rtmp, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    }
     if (rc) return rc;
     return copy_out(c, R_out, c->d_Rtmp, (size_t)c->n * 8, out_on_device);
 }
@@ -502,7 +553,11 @@ int ust_sample_trees(ust_ctx *h, int64_t t0, int32_t count, uint64_t seed, int32
         cudaFree(d_next);
         return ust::fail(c, UST_ENOMEM, "tree export buffer");
     }
-    int rc = ust::run_sampler(c, t0, t0 + count, seed, nullptr, d_next, d_pops, nullptr, nullptr, nullptr, nullptr);
+    int rc;
+    {
+        SamplingRows rows(c);
+        rc = ust::run_sampler(c, t0, t0 + count, seed, nullptr, d_next, d_pops, nullptr, nullptr, nullptr, nullptr);
+    }
     if (!rc) rc = copy_out(c, next_out, d_next, elems * 4, 0);
     if (!rc && pops_out) rc = copy_out(c, pops_out, d_pops, elems * 4, 0);
     cudaFree(d_next);

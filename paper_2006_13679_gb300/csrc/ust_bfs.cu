@@ -215,6 +215,200 @@ __global__ void min_bound_kernel(int n, const int32_t *__restrict__ lb, unsigned
     atomicMin(best, b);
 }
 
+
+// ---- biconnected-component variant (Appendix D) ---------------------------
+// Rows of the block-restricted sampler: v != u keeps its neighbours inside its
+// parent block, the block of the tree edge e(v) = (bfs_parent(v), v) of B_u.
+// Blocks are labelled by Tarjan and Vishkin's rules over B_u (any rooted
+// spanning tree serves). With preorder numbers pre, subtree sizes nd, and
+// lo(v) / hi(v) the least / largest pre reached from v's subtree by a
+// non-tree edge (pre(v) itself included), tree edges share a block when
+//   (1) a non-tree edge (v, w) joins two unrelated subtrees: e(v) ~ e(w);
+//   (2) p = bfs_parent(v) != u and v's subtree reaches outside p's subtree
+//       (lo(v) < pre(p) or hi(v) >= pre(p) + nd(p)): e(v) ~ e(p).
+// A non-tree edge lies in the block of e(x), x its endpoint of larger pre.
+// Preorder and sizes follow the BFS levels, one launch per level.
+
+__device__ __forceinline__ bool tree_edge(int v, int w, const int32_t *__restrict__ bpar)
+{
+    return bpar[w] == v || bpar[v] == w;
+}
+
+__global__ void bt_init_kernel(int n, int u, int32_t *nd, int32_t *pre, int32_t *cur, int32_t *uf)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        nd[v] = 1;
+        pre[v] = 0;
+        cur[v] = (v == u) ? 1 : 0;
+        uf[v] = v;
+    }
+}
+
+// Subtree sizes, deepest level first: nd[v] is complete when v's level runs.
+__global__ void bt_size_kernel(int n, int level, const int32_t *__restrict__ dist,
+                               const int32_t *__restrict__ bpar, int32_t *nd)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (dist[v] == level) atomicAdd(nd + bpar[v], nd[v]);
+}
+
+// Preorder numbers, top level first: a child takes the next free interval of
+// its parent's (any child order is a preorder).
+__global__ void bt_pre_kernel(int n, int level, const int32_t *__restrict__ dist,
+                              const int32_t *__restrict__ bpar, const int32_t *__restrict__ nd, int32_t *pre,
+                              int32_t *cur)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (dist[v] != level) continue;
+        const int p = atomicAdd(cur + bpar[v], nd[v]);
+        pre[v] = p;
+        cur[v] = p + 1;
+    }
+}
+
+__global__ void bt_local_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre, int32_t *lo,
+                                int32_t *hi)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int l = pre[v], h = pre[v];
+        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+            const int w = ci[e];
+            if (tree_edge(v, w, bpar)) continue;
+            l = min(l, pre[w]);
+            h = max(h, pre[w]);
+        }
+        lo[v] = l;
+        hi[v] = h;
+    }
+}
+
+// lo / hi over subtrees, deepest level first.
+__global__ void bt_lohi_kernel(int n, int level, const int32_t *__restrict__ dist,
+                               const int32_t *__restrict__ bpar, int32_t *lo, int32_t *hi)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (dist[v] != level) continue;
+        atomicMin(lo + bpar[v], lo[v]);
+        atomicMax(hi + bpar[v], hi[v]);
+    }
+}
+
+// Union-find over tree edges (named by their child vertex): roots are only
+// hooked under smaller roots, finds halve paths. Reads bypass L1 so that a
+// hook by another SM is seen; every loop is bounded and flags *bad.
+__device__ int uf_find(int32_t *uf, int x, int n, int *bad)
+{
+    for (int k = 0; k <= n; ++k) {
+        const int p = __ldcg(uf + x);
+        if (p == x) return x;
+        const int g = __ldcg(uf + p);
+        if (g == p) return p;
+        uf[x] = g;  // x is no root: any ancestor is a valid parent
+        x = g;
+    }
+    atomicExch(bad, 1);
+    return x;
+}
+
+__device__ void uf_union(int32_t *uf, int a, int b, int n, int *bad)
+{
+    for (int k = 0; k <= n; ++k) {
+        a = uf_find(uf, a, n, bad);
+        b = uf_find(uf, b, n, bad);
+        if (a == b) return;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(uf + b, b, a) == b) return;
+    }
+    atomicExch(bad, 1);
+}
+
+__global__ void bt_rule1_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
+                                const int32_t *__restrict__ nd, int32_t *uf, int *bad)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int pv = pre[v], end = pv + nd[v];
+        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+            const int w = ci[e];
+            if (tree_edge(v, w, bpar)) continue;
+            const int pw = pre[w];
+            if (pv < pw && pw >= end) uf_union(uf, v, w, n, bad);
+        }
+    }
+}
+
+__global__ void bt_rule2_kernel(int n, int u, const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
+                                const int32_t *__restrict__ nd, const int32_t *__restrict__ lo,
+                                const int32_t *__restrict__ hi, int32_t *uf, int *bad)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (v == u) continue;
+        const int p = bpar[v];
+        if (p == u) continue;
+        if (lo[v] < pre[p] || hi[v] >= pre[p] + nd[p]) uf_union(uf, v, p, n, bad);
+    }
+}
+
+__global__ void bt_label_kernel(int n, int32_t *uf, int32_t *lab, int *bad)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        lab[v] = uf_find(uf, v, n, bad);
+}
+
+__device__ __forceinline__ int block_of(int v, int w, const int32_t *__restrict__ bpar,
+                                        const int32_t *__restrict__ pre, const int32_t *__restrict__ lab)
+{
+    if (bpar[w] == v) return lab[w];
+    if (bpar[v] == w) return lab[v];
+    return pre[v] > pre[w] ? lab[v] : lab[w];
+}
+
+__global__ void wk_count_kernel(int n, int u, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
+                                const int32_t *__restrict__ lab, int32_t *wdeg)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int c = 0;
+        if (v != u) {
+            const int pb = lab[v];
+            for (int e = rp[v]; e < rp[v + 1]; ++e) c += (block_of(v, ci[e], bpar, pre, lab) == pb);
+        }
+        wdeg[v] = c;
+    }
+}
+
+__global__ void wk_fill_kernel(int n, int u, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
+                               const int32_t *__restrict__ lab, const int32_t *__restrict__ wrp, int32_t *wci,
+                               int32_t *wmap)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (v == u) continue;
+        const int pb = lab[v];
+        int o = wrp[v];
+        const int o1 = wrp[v + 1];
+        for (int e = rp[v]; e < rp[v + 1] && o < o1; ++e) {
+            const int w = ci[e];
+            if (block_of(v, w, bpar, pre, lab) != pb) continue;
+            wci[o] = w;
+            wmap[o] = e;
+            ++o;
+        }
+    }
+}
+
+__global__ void wk_scatter_kernel(int64_t wnnz, const int32_t *__restrict__ wmap, const int64_t *__restrict__ src,
+                                  int64_t *dst)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < wnnz; j += (int64_t)gridDim.x * blockDim.x)
+        dst[wmap[j]] = src[j];
+}
+
 }  // namespace
 
 int select_pivot(Ctx *c, int n, const int32_t *d_rp, const int32_t *d_ci, int sweeps, int start, int32_t *pivot,
@@ -415,6 +609,90 @@ int run_bfs(Ctx *c)
     path_fill_kernel<<<blocks, threads, 0, c->stream>>>(n, c->pivot, c->d_bpar, c->d_pathptr, c->d_path,
                                                         c->d_path + c->path_cap, c->d_path + 2 * c->path_cap);
     c->launches += 2;
+    UST_CUDA_TRY(cudaGetLastError());
+    return UST_OK;
+}
+
+
+int build_block_rows(Ctx *c)
+{
+    const int n = c->n, u = c->pivot;
+    if (!c->d_wrp) {
+        if (cudaMalloc(&c->d_wrp, ((size_t)n + 1) * 4) != cudaSuccess ||
+            cudaMalloc(&c->d_wci, (size_t)c->nnz * 4) != cudaSuccess ||
+            cudaMalloc(&c->d_wmap, (size_t)c->nnz * 4) != cudaSuccess)
+            return fail(c, UST_ENOMEM, "block-restricted rows");
+    }
+    int32_t *s = nullptr;
+    if (cudaMalloc(&s, 6 * (size_t)n * 4) != cudaSuccess) return fail(c, UST_ENOMEM, "block labels");
+    int32_t *nd = s, *pre = s + n, *cur = s + 2 * (size_t)n, *lo = s + 3 * (size_t)n, *hi = s + 4 * (size_t)n,
+            *uf = s + 5 * (size_t)n;
+    int32_t *lab = cur, *wdeg = lo;  // cur and lo are free again by then
+    int *d_bad = c->d_flag;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    cudaStream_t st = c->stream;
+    int rc = UST_OK;
+    int64_t launches = 0;
+#define BT_TRY(call)                                                                     \
+    do {                                                                                 \
+        const cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                         \
+            rc = fail(c, UST_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            goto done;                                                                   \
+        }                                                                                \
+    } while (0)
+    BT_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    bt_init_kernel<<<blocks, threads, 0, st>>>(n, u, nd, pre, cur, uf);
+    ++launches;
+    for (int level = c->ecc; level >= 1; --level, ++launches)
+        bt_size_kernel<<<blocks, threads, 0, st>>>(n, level, c->d_dist, c->d_bpar, nd);
+    for (int level = 1; level <= c->ecc; ++level, ++launches)
+        bt_pre_kernel<<<blocks, threads, 0, st>>>(n, level, c->d_dist, c->d_bpar, nd, pre, cur);
+    bt_local_kernel<<<blocks, threads, 0, st>>>(n, c->d_rp, c->d_ci, c->d_bpar, pre, lo, hi);
+    ++launches;
+    for (int level = c->ecc; level >= 1; --level, ++launches)
+        bt_lohi_kernel<<<blocks, threads, 0, st>>>(n, level, c->d_dist, c->d_bpar, lo, hi);
+    bt_rule1_kernel<<<blocks, threads, 0, st>>>(n, c->d_rp, c->d_ci, c->d_bpar, pre, nd, uf, d_bad);
+    bt_rule2_kernel<<<blocks, threads, 0, st>>>(n, u, c->d_bpar, pre, nd, lo, hi, uf, d_bad);
+    bt_label_kernel<<<blocks, threads, 0, st>>>(n, uf, lab, d_bad);
+    wk_count_kernel<<<blocks, threads, 0, st>>>(n, u, c->d_rp, c->d_ci, c->d_bpar, pre, lab, wdeg);
+    path_offsets_kernel<<<1, kScanThreads, 0, st>>>(n, wdeg, c->d_wrp);
+    wk_fill_kernel<<<blocks, threads, 0, st>>>(n, u, c->d_rp, c->d_ci, c->d_bpar, pre, lab, c->d_wrp, c->d_wci,
+                                               c->d_wmap);
+    launches += 6;
+    BT_TRY(cudaGetLastError());
+    {
+        int32_t *h = reinterpret_cast<int32_t *>(c->h_stats);
+        BT_TRY(cudaMemcpyAsync(h, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BT_TRY(cudaMemcpyAsync(h + 1, c->d_wrp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        BT_TRY(cudaStreamSynchronize(st));
+        if (h[0] != 0) {
+            rc = fail(c, UST_ECUDA, "block labels: union-find bound reached");
+            goto done;
+        }
+        if (h[1] < n - 1 || h[1] > c->nnz) {
+            rc = fail(c, UST_ECUDA, "block-restricted rows: inconsistent arc count");
+            goto done;
+        }
+        c->wnnz = h[1];
+    }
+done:
+#undef BT_TRY
+    c->launches += launches;
+    cudaStreamSynchronize(st);
+    cudaFree(s);
+    return rc;
+}
+
+int scatter_block_counts(Ctx *c, const int64_t *d_walk_counts, int64_t *d_out)
+{
+    UST_CUDA_TRY(cudaMemsetAsync(d_out, 0, (size_t)c->nnz * sizeof(int64_t), c->stream));
+    const int threads = 256;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((c->wnnz + threads - 1) / threads,
+                                                                   (int64_t)c->num_sms * 8));
+    wk_scatter_kernel<<<blocks, threads, 0, c->stream>>>(c->wnnz, c->d_wmap, d_walk_counts, d_out);
+    c->launches += 1;
     UST_CUDA_TRY(cudaGetLastError());
     return UST_OK;
 }

@@ -118,6 +118,12 @@ struct Ctx {
     int32_t *d_flag = nullptr;  // BFS level flag and misc small device scalars
     int32_t *d_pathptr = nullptr, *d_path = nullptr;  // flattened BFS paths P(v): 3 x path_cap (ancestor, child, owner)
     int64_t path_cap = 0;
+    // biconnected-component variant (ust_opts.wilson_blocks): the rows the
+    // walks draw from, v's neighbours in its parent block, and each row
+    // entry's arc in the input CSR
+    bool blocks = false;
+    int32_t *d_wrp = nullptr, *d_wci = nullptr, *d_wmap = nullptr;
+    int64_t wnnz = 0;
 
     // sampling
     LaunchCfg cfg;                  // single graph: the sampler's launch shape
@@ -217,6 +223,10 @@ inline void phase_close(Ctx *c, int ph)
 
 // Host drivers (one per translation unit).
 int run_bfs(Ctx *c);
+// The walk rows of the biconnected-component variant for the current B_u.
+int build_block_rows(Ctx *c);
+// Arc counts of the variant's walk rows, scattered to the input CSR's arcs.
+int scatter_block_counts(Ctx *c, const int64_t *d_walk_counts, int64_t *d_out);
 // The input checks of ust_init on a device CSR; d_bad: one int of scratch.
 int check_graph(Ctx *c, int n, int nnz, const int32_t *d_rp, const int32_t *d_ci, int *d_bad);
 // Pivot by eccentricity lower bounds from `sweeps` double-sweep BFS runs

@@ -410,3 +410,84 @@ def test_select_pivot_rejects_disconnected(pkg):
     with pytest.raises(pkg.UstError) as e:
         pkg.select_pivot(g.row_ptr, g.col_idx)
     assert e.value.code == pkg.UST_ENOTCONNECTED
+
+
+# ------------------------------------------- biconnected-component variant
+
+def _block_example():
+    src = [0, 1, 0, 2, 3, 2, 4, 5, 6, 4, 7]
+    dst = [1, 2, 2, 3, 4, 4, 5, 6, 7, 7, 8]
+    return synth.from_edges(9, src, dst, lcc=False)
+
+
+BLOCK_GRAPHS = {
+    "example": lambda: (_block_example(), 5),
+    "tree": lambda: (lambda g: (g, synth.max_degree_vertex(g)))(synth.ba(500, 1, seed=4)),
+    "er_sparse": lambda: (lambda g: (g, synth.max_degree_vertex(g)))(synth.er(3000, 2.5, seed=7)),
+    "rmat12": GRAPHS["rmat12"],
+    "ba3000": GRAPHS["ba3000"],
+}
+
+
+@pytest.mark.parametrize("name", sorted(BLOCK_GRAPHS))
+def test_block_variant_bit_exact(pkg, orc, name):
+    """wilson_blocks: the device's Tarjan-Vishkin rows give the same trees,
+    counts and draws as the oracle's Hopcroft-Tarjan rows."""
+    g, u = BLOCK_GRAPHS[name]()
+    w = orc.parent_block_graph(g, u)
+    _, _, par = orc.bfs(g, u)
+    with make(pkg, g, u, wilson_blocks=True) as h:
+        h.sample_aggregate(300, 31)
+        R_ref, steps = orc.sample_aggregate(w, u, par, 0, 300, 31, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert h.info()["draws"] == steps
+        nxt, pops = h.sample_trees(10, 3, 31, with_pops=True)
+        for i in range(3):
+            ref, ref_pops, _ = orc.wilson(w, u, 10 + i, 31)
+            assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
+
+
+def test_block_variant_on_one_block_equals_plain_wilson(pkg, orc):
+    """A grid is one block: the restricted rows are the full rows (the root's
+    is unused), so the trees are plain Wilson's."""
+    g, u = synth.grid(12, 12), 78
+    with make(pkg, g, u, wilson_blocks=True) as a, make(pkg, g, u) as b:
+        a.sample_aggregate(200, 5)
+        b.sample_aggregate(200, 5)
+        assert np.array_equal(a.counts(), b.counts())
+
+
+def test_block_variant_reset_and_edge_counts(pkg, orc):
+    """ust_reset rebuilds the rows for the new pivot; arc counts are reported
+    per arc of the input graph."""
+    g = synth.er(2000, 3.0, seed=11)
+    u0, u1 = synth.max_degree_vertex(g), 17
+    with make(pkg, g, u0, wilson_blocks=True) as h:
+        h.sample_aggregate(50, 2)
+        h.reset(u1)
+        h.track_edges(True)
+        h.sample_aggregate(120, 9)
+        w = orc.parent_block_graph(g, u1)
+        _, _, par = orc.bfs(g, u1)
+        R_ref, _ = orc.sample_aggregate(w, u1, par, 0, 120, 9, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert np.array_equal(h.edge_counts(), orc.edge_counts(g, u1, 0, 120, 9, walk=w))
+
+
+def test_block_variant_rmat16_full(pkg, orc):
+    """The bench workload (R-MAT16, 4096 trees) with the variant."""
+    g, u, T, _ = synth.workload("rmat16")
+    w = orc.parent_block_graph(g, u)
+    _, _, par = orc.bfs(g, u)
+    with make(pkg, g, u, wilson_blocks=True) as h:
+        h.sample_aggregate(T, 0)
+        R_ref, steps = orc.sample_aggregate(w, u, par, 0, T, 0, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert h.info()["draws"] == steps
+
+
+def test_block_variant_rejected_for_batches(pkg):
+    gs = [synth.grid(4, 4), synth.cycle(10)]
+    with pytest.raises(pkg.UstError) as ei:
+        pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], [0, 0], wilson_blocks=True)
+    assert ei.value.code == pkg.UST_EINVAL
