@@ -235,6 +235,12 @@ UST_API int ust_centralities(ust_ctx *c, double eps, double *closeness_out, doub
 /* Sample size tau(eps) of Algorithm 1 for this graph and pivot. */
 UST_API int64_t ust_tau(const ust_ctx *c, double eps);
 
+/* Trees aggregated in R so far: tau of the combination in Algorithm 1 (the
+ * committed count; a failed call leaves it unchanged, ust_set_counts sets
+ * it, ust_reset clears it). A batch: the least count over its graphs
+ * (ust_batch_graph_info gives each graph's). -1 for a NULL context. */
+UST_API int64_t ust_num_trees(const ust_ctx *c);
+
 /* R[v] as exact integers (n int64). */
 UST_API int ust_get_counts(ust_ctx *c, int64_t *R_out, int32_t out_on_device);
 

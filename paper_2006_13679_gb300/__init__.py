@@ -137,6 +137,10 @@ class UST:
     def tau(self, eps: float) -> int:
         return int(load().ust_tau(self._h, float(eps)))
 
+    def num_trees(self) -> int:
+        """``ust_num_trees``: trees aggregated in R so far."""
+        return int(load().ust_num_trees(self._h))
+
     def _out(self, out, dtype, count):
         if out is None:
             out = np.empty(count, dtype=dtype)
@@ -265,6 +269,7 @@ class USTBatch:
     sample_aggregate = UST.sample_aggregate
     set_counts = UST.set_counts
     tau = UST.tau
+    num_trees = UST.num_trees
     _out = UST._out
     diag = UST.diag
     centralities = UST.centralities

@@ -76,6 +76,7 @@ _SIGNATURES = {
                                         ctypes.c_void_p, ctypes.c_int32]),
     "ust_diag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int32]),
     "ust_tau": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_double]),
+    "ust_num_trees": (ctypes.c_int64, [ctypes.c_void_p]),
     "ust_get_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "ust_track_edges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "ust_get_edge_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),

@@ -378,6 +378,16 @@ int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
     return UST_OK;
 }
 
+int64_t ust_num_trees(const ust_ctx *h)
+{
+    if (!h) return -1;
+    const Ctx *c = &h->c;
+    if (!c->batch) return c->trees;
+    int64_t least = c->btrees.empty() ? 0 : c->btrees[0];
+    for (const int64_t t : c->btrees) least = std::min(least, t);
+    return least;
+}
+
 int64_t ust_tau(const ust_ctx *h, double eps)
 {
     if (!h || !(eps > 0)) return 0;

@@ -56,6 +56,7 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.ust_strerror(-5) == b"UST_ETIMEOUT"
     lib.ust_free(None)
     assert lib.ust_tau(None, 0.3) == 0
+    assert lib.ust_num_trees(None) == -1
 
 
 def test_product_package_does_not_import_the_oracle():

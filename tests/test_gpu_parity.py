@@ -109,6 +109,7 @@ def test_calls_continue_tree_ids(pkg, orc):
             b.sample_aggregate(k, 9)
         assert np.array_equal(a.counts(), b.counts())
         assert a.info()["trees"] == b.info()["trees"] == 37
+        assert a.num_trees() == b.num_trees() == 37
         _, _, par = orc.bfs(g, u)
         R_ref, _ = orc.sample_aggregate(g, u, par, 0, 37, 9)
         assert np.array_equal(a.counts(), R_ref)
