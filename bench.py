@@ -437,8 +437,17 @@ def cpu_baseline(g, u, T, sample, wilson_blocks: bool = False) -> dict:
     what = "one full step" if sample == T else f"BFS + {sample} of the {T} trees"
     if wilson_blocks:
         what += " on the parent-block rows (built outside the timed step)"
+    # the sequential oracle on one core, over a share of the sample that
+    # takes about as long as the run above
+    k = max(1, min(sample, sample // max(1, threads)))
+    t1 = time.perf_counter()
+    _, _, par1 = oracle.bfs(g, u)
+    oracle.sample_aggregate(walk, u, par1, 0, k, SEED, threads=1)
+    sec1 = time.perf_counter() - t1
     return {"value": sample / sec, "unit": "trees/s", "cores": threads, "kind": "oracle",
-            "sample": f"{what} + FP64 CG + combine, OpenMP over trees", "seconds": sec}
+            "sample": f"{what} + FP64 CG + combine, OpenMP over trees", "seconds": sec,
+            "one_core": {"value": k / sec1, "unit": "trees/s", "trees": k,
+                         "sample": f"BFS + {k} trees, sequential (the sampling loop of Algorithm 1)"}}
 
 
 def main() -> None:
