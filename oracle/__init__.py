@@ -14,8 +14,10 @@ Two layers:
 * numpy/scipy helpers in this file: the dense closed form
   L^+ = (L + J/n)^{-1} - J/n (Section 2.1), effective resistances from it
   (Eq. eff-res), brute-force spanning-tree enumeration and the matrix-tree
-  count, which pin the C layer in the tests; and the centralities that
-  depend only on the diagonal (closeness, NRWB, Kirchhoff index).
+  count, which pin the C layer in the tests; the centralities that
+  depend only on the diagonal (closeness, NRWB, Kirchhoff index); and, for
+  the biconnected-component variant of Appendix D, the blocks (Hopcroft and
+  Tarjan's search) and the parent-block rows the walks draw from.
 """
 from __future__ import annotations
 
