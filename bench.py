@@ -42,6 +42,8 @@ TRAFFIC_CAPTURE = {"workload": "rmat16", "sha1": "7ded4869447e46db18d7397ada8455
 WORKLOADS = {
     "rmat16": ("R-MAT scale 16, edge factor 16, (0.57,0.19,0.19,0.05), LCC, max-degree pivot, 4096 trees", None),
     "grid48": ("48x48 4-neighbour grid, pivot (24,24), 1000 trees", None),
+    "rmat17": ("R-MAT scale 17, edge factor 16, LCC, max-degree pivot, 1024 trees (a small case of the "
+               "large-graph sampler, for profiling)", None),
     "hyperbolic20": ("random hyperbolic graph n=2^20, avg degree 20, exponent 3, T=0, LCC, max-degree pivot, "
                      "tau(eps=0.3)", 256),
     "rmat22": ("R-MAT scale 22, edge factor 16, LCC, max-degree pivot, tau(eps=0.3)", 96),
@@ -68,6 +70,16 @@ BYTES_PER_PAIR = 16
 
 def algorithmic_bytes(draws: int, trees: int, n: int, farness: int) -> int:
     return BYTES_PER_DRAW * draws + trees * (BYTES_PER_VERTEX * n + BYTES_PER_PAIR * farness)
+
+
+def phase_names(n: int):
+    """Names of the sampler's per-tree cycle counters (thread 0's clock per
+    phase), which depend on the kernel that serves a graph of n vertices."""
+    if n <= 0xFFFF:
+        return ["first_draws", "in_degrees", "leaf_queue", "peeling", "cycle_list", "pop_rounds", "child_counts",
+                "sizes_offsets", "preorder", "aggregation", "tree_total"]
+    return ["first_draws", "in_degrees", "peeling_cycle_list", "pop_rounds", "sizes_offsets", "preorder",
+            "aggregation", "tree_total"]
 
 
 def peaks():
@@ -462,6 +474,8 @@ def main() -> None:
     ap.add_argument("--wilson-blocks", action="store_true",
                     help="single-graph workloads: walks inside each vertex's parent block "
                          "(the biconnected-component variant)")
+    ap.add_argument("--trees", type=int, default=0,
+                    help="single-graph workloads: trees per step instead of the workload's own count")
     ap.add_argument("--per-class", action="store_true",
                     help="batch256: also time each size class of the batch on its own")
     ap.add_argument("--no-comparator", action="store_true",
@@ -496,7 +510,7 @@ def main() -> None:
         run_batch_gpu(args, rank, world, local_rank, dist)
         return
     g, u, T0, eps = synth.workload(args.workload)
-    T = workload_trees(g, u, T0, eps)
+    T = args.trees if args.trees > 0 else workload_trees(g, u, T0, eps)
     seed = SEED
     stream = torch.cuda.Stream()
     rp_d = torch.from_numpy(g.row_ptr).cuda()
@@ -626,9 +640,7 @@ def main() -> None:
                                      else "plain Wilson rooted at the pivot")},
                 "diag_ms": ms, "phase_ms": {"bfs": statistics.mean(bfs_ms), "sample_kernel": kernel_ms,
                                             "solve": statistics.mean(solve_ms)},
-                "sampler_cycles_per_tree": dict(zip(["first_draws", "in_degrees", "leaf_queue", "peeling",
-                                                     "cycle_list", "pop_rounds", "child_counts", "sizes_offsets",
-                                                     "preorder", "aggregation", "tree_total"],
+                "sampler_cycles_per_tree": dict(zip(phase_names(g.n),
                                                     [c / max(1, info["last_trees"]) for c in info["last_phase_cycles"]])),
                 "draws_per_tree": statistics.mean(draws) / T, "cg_iters": info["cg_iters"],
                 "cg_refinements": info["cg_refinements"], "cg_relres": info["cg_relres"],

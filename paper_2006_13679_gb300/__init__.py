@@ -17,7 +17,7 @@ from ._binding import (UST_EINVAL, UST_ENOMEM, UST_ENOTCONNECTED, UST_ENOTCONVER
                        UST_ETIMEOUT, UST_OK, UstError, check, load)
 from ._build import LIB as LIB_PATH
 
-__all__ = ["UST", "USTBatch", "select_pivot", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
+__all__ = ["UST", "USTBatch", "select_pivot", "probe_random_access", "build", "load", "UstError", "LIB_PATH", "UST_OK", "UST_EINVAL", "UST_ENOTCONNECTED",
            "UST_ENOMEM", "UST_ETIMEOUT", "UST_ENOTCONVERGED", "UST_ESTATE"]
 
 
@@ -66,6 +66,16 @@ def select_pivot(row_ptr, col_idx, sweeps: int = 10, start: int = -1, stream=Non
     piv, bound = ctypes.c_int32(), ctypes.c_int32()
     check(L.ust_select_pivot(ctypes.byref(g), int(sweeps), int(start), sh, ctypes.byref(piv), ctypes.byref(bound)))
     return int(piv.value), int(bound.value)
+
+
+def probe_random_access(nbytes: int, mode: int = 0, reps: int = 3, stream=None) -> float:
+    """``ust_probe_random_access``: random 4-byte accesses per second over a
+    device array of ``nbytes`` (mode 0 loads through L2, mode 1 atomics)."""
+    out = ctypes.c_double()
+    rc = load().ust_probe_random_access(int(nbytes), int(mode), int(reps), _stream_handle(stream), ctypes.byref(out))
+    if rc != 0:
+        raise UstError(rc, "random-access probe failed")
+    return float(out.value)
 
 
 class UST:

@@ -90,6 +90,8 @@ _SIGNATURES = {
     "ust_tree_counts_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "ust_probe_random_access": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.POINTER(ctypes.c_double)]),
     "ust_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ust_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ust_free": (None, [ctypes.c_void_p]),

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libust.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["ust_api.cu", "ust_batch.cu", "ust_bfs.cu", "ust_wilson.cu", "ust_solve.cu", "ust_solve_cta.cu", "ust_centrality.cu"]
+SOURCES = ["ust_api.cu", "ust_batch.cu", "ust_bfs.cu", "ust_wilson.cu", "ust_solve.cu", "ust_solve_cta.cu", "ust_centrality.cu", "ust_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -32,7 +32,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    files.append(os.path.join(INCLUDE, "ust.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     files.append(os.path.abspath(__file__))
     return files
 

@@ -297,6 +297,9 @@ def workload(name: str):
 
     grid48      48x48 grid, pivot (24, 24) = 1176, 1000 trees
     rmat16      R-MAT scale 16, edge factor 16, LCC, max-degree pivot, 4096 trees
+    rmat17      R-MAT scale 17, edge factor 16, LCC, max-degree pivot, 1024 trees
+                (the smallest R-MAT above 65,535 vertices: a profiling case
+                of the large-graph sampler)
     hyperbolic20  threshold RHG n = 2^20, avg degree 20, gamma 3, eps 0.3
     rmat22      R-MAT scale 22, edge factor 16, LCC, max-degree pivot, eps 0.3
     """
@@ -305,6 +308,9 @@ def workload(name: str):
     if name == "rmat16":
         g = rmat(16, 16, seed=1)
         return g, max_degree_vertex(g), 4096, None
+    if name == "rmat17":
+        g = rmat(17, 16, seed=1)
+        return g, max_degree_vertex(g), 1024, None
     if name == "rmat22":
         g = rmat(22, 16, seed=1)
         return g, max_degree_vertex(g), None, 0.3

@@ -1,4 +1,4 @@
-"""The C ABI library loads and exports every entry point include/ust.h
+"""The C ABI library loads and exports every entry point include/*.h
 declares; argument checks that need no GPU. No compute calls here."""
 import ctypes
 import os
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "ust.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*UST_API\s+(?:const\s+)?[a-z_0-9]+\s*\*?\s*(ust_[a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
