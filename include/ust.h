@@ -108,6 +108,13 @@ typedef struct {
                                with B_u (ust_init, ust_reset); arc counts stay per input arc.
                                Single-graph contexts only (ust_init_batch: UST_EINVAL)
                                [0 = plain Wilson rooted at u] */
+    int32_t autotune;       /* launch shapes of the sampler: 1 = tuned, -1 = fixed table, 0 = default
+                               [tuned for ust_init_batch, fixed for ust_init]. Tuning times every
+                               candidate shape (threads per CTA x CTAs per SM that fit) on a probe of
+                               the launch's own work at context creation and keeps the fastest; the
+                               choice is remembered for the process per workload key (kernel, size
+                               class, average and pivot degree, graph count). block_threads /
+                               ctas_per_sm, when set, override it. Counts do not depend on the shape. */
     void *stream;           /* cudaStream_t to issue work on [NULL = legacy default stream] */
 } ust_opts;
 
@@ -198,10 +205,13 @@ UST_API int ust_batch_graph_info(const ust_ctx *c, int32_t g, ust_info *out);
 
 /* Re-targets the context to pivot u = pivot on the same graph: recomputes
  * B_u, ecc(u) and f^c(u) and clears R, the tree count and the cached column
- * (Algorithm 1 from its first line). No allocation, except with
- * wilson_blocks: the walk rows are rebuilt for the new B_u with 24 bytes per
- * vertex of temporary device memory. A batch context keeps its pivots:
- * pivot must be -1 there. Errors: UST_EINVAL, UST_ENOMEM (wilson_blocks),
+ * (Algorithm 1 from its first line); with wilson_blocks the walk rows are
+ * rebuilt for the new B_u (in scratch allocated by ust_init). It allocates
+ * only when the new pivot's f^c(u) exceeds the flattened-path space the
+ * context holds (12 bytes per entry, 16 above 65,535 vertices). A batch
+ * context keeps its pivots: pivot must be -1 there. If the call fails after
+ * its argument checks, the context refuses every sampling call with
+ * UST_ESTATE until a ust_reset succeeds. Errors: UST_EINVAL, UST_ENOMEM,
  * UST_ECUDA. */
 UST_API int ust_reset(ust_ctx *c, int32_t pivot);
 
@@ -309,8 +319,11 @@ UST_API int ust_get_info(const ust_ctx *c, ust_info *out);
  *
  * All scratch lives in one fixed device array inside the library (about
  * 10.6 MB, held on every GPU that loads the library until the process exits).
- * Limits: n <= 4096 and f^c(u) = sum_v dist(u, v) <= 262144; larger inputs
- * return UST_EINVAL before any work. The first call on a device looks up the
+ * Limits: n <= 4096 and f^c(u) = sum_v dist(u, v) <= 262144. A larger n
+ * returns UST_EINVAL before any work; f^c(u) is known only once B_u has been
+ * computed, in the scratch array, so a larger f^c(u) returns UST_EINVAL (and
+ * a graph that is not connected UST_ENOTCONNECTED) after that step. In every
+ * error case R_out is left untouched. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. Every call reuses the same
  * array and overwrites what the previous call left there, so calls that can

@@ -23,12 +23,15 @@ extern "C" {
 #endif
 
 /* Times `reps` launches (after one warm-up launch that also pulls an
- * L2-sized array into L2) of random 4-byte accesses over a device array of
+ * L2-sized array into L2) of random accesses over a device array of
  * the largest power-of-two size that fits `bytes` (1 MiB to 64 GiB):
- *   mode 0: loads that bypass L1 (ld.global.cg), served by L2 or DRAM;
- *   mode 1: atomicAdd of 1 (performed in L2).
+ *   mode 0: 4-byte loads that bypass L1 (ld.global.cg), served by L2 or DRAM;
+ *   mode 1: 4-byte atomicAdd of 1 (performed in L2);
+ *   modes 2, 3, 4: aligned blocks of 16, 32 or 64 bytes, read as 16-byte
+ *   vector loads that bypass L1 (the cost of a random access by its width).
  * 2048 threads per SM each keep 8 independent accesses in flight.
- * *accesses_per_s receives the best launch's accesses per second. The array
+ * *accesses_per_s receives the best launch's accesses (4-byte words or
+ * blocks) per second. The array
  * is allocated and freed by the call (cudaMalloc / cudaFree); work runs on
  * `stream` (a cudaStream_t, NULL = legacy default stream), which the call
  * synchronises. Returns 0, -1 (bad argument), -3 (allocation failed) or

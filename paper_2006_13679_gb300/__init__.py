@@ -90,7 +90,7 @@ class UST:
     def __init__(self, row_ptr, col_idx, pivot: int, *, delta: float = 0.0, kappa: float = 0.3,
                  cg_tol: float = 1e-9, max_pop_rounds: int = 0, max_cg_iters: int = 0, graph_id: int = 0,
                  block_threads: int = 0, ctas_per_sm: int = 0, stream=None, skip_validation: bool = False,
-                 solve_fp64: bool = False, wilson_blocks: bool = False):
+                 solve_fp64: bool = False, wilson_blocks: bool = False, autotune: int = 0):
         L = load()
         self._keep = []
         rp = row_ptr if _is_torch(row_ptr) else np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -109,6 +109,7 @@ class UST:
         o.graph_id, o.block_threads, o.ctas_per_sm = graph_id, block_threads, ctas_per_sm
         o.solve_fp64 = int(bool(solve_fp64))
         o.wilson_blocks = int(bool(wilson_blocks))
+        o.autotune = int(autotune)
         sh = _stream_handle(stream)
         o.stream = sh.value if sh is not None else None
         h = ctypes.c_void_p()
@@ -237,7 +238,7 @@ class USTBatch:
     def __init__(self, graphs, pivots, *, delta: float = 0.0, kappa: float = 0.3, cg_tol: float = 1e-9,
                  max_pop_rounds: int = 0, max_cg_iters: int = 0, graph_id: int = 0, block_threads: int = 0,
                  ctas_per_sm: int = 0, stream=None, skip_validation: bool = False, solve_fp64: bool = False,
-                 wilson_blocks: bool = False):
+                 wilson_blocks: bool = False, autotune: int = 0):
         L = load()
         self._keep = []
         csrs = (_binding.ust_csr * len(graphs))()
@@ -256,6 +257,7 @@ class USTBatch:
         o.graph_id, o.block_threads, o.ctas_per_sm = graph_id, block_threads, ctas_per_sm
         o.solve_fp64 = int(bool(solve_fp64))
         o.wilson_blocks = int(bool(wilson_blocks))  # single-graph contexts only: UST_EINVAL here
+        o.autotune = int(autotune)
         sh = _stream_handle(stream)
         o.stream = sh.value if sh is not None else None
         h = ctypes.c_void_p()

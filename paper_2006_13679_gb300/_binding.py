@@ -33,7 +33,8 @@ class ust_opts(ctypes.Structure):
                 ("max_pop_rounds", ctypes.c_int32), ("max_cg_iters", ctypes.c_int32),
                 ("skip_validation", ctypes.c_int32), ("graph_id", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("solve_fp64", ctypes.c_int32), ("wilson_blocks", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("solve_fp64", ctypes.c_int32), ("wilson_blocks", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class ust_info(ctypes.Structure):

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libust.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["ust_api.cu", "ust_batch.cu", "ust_bfs.cu", "ust_wilson.cu", "ust_solve.cu", "ust_solve_cta.cu", "ust_centrality.cu", "ust_probe.cu"]
+SOURCES = ["ust_api.cu", "ust_batch.cu", "ust_bfs.cu", "ust_wilson.cu", "ust_solve.cu", "ust_solve_cta.cu", "ust_centrality.cu", "ust_probe.cu",
+           "ust_relabel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -37,6 +37,12 @@ void release(Ctx *c)
     cudaFree(c->d_wrp);
     cudaFree(c->d_wci);
     cudaFree(c->d_wmap);
+    cudaFree(c->d_bscratch);
+    cudaFree(c->d_srp);
+    cudaFree(c->d_sci);
+    cudaFree(c->d_orig);
+    cudaFree(c->d_newid);
+    cudaFree(c->d_spath);
     cudaFree(c->d_ws);
     cudaFree(c->d_Rp);
     cudaFree(c->d_R);
@@ -104,6 +110,41 @@ int apply_opts(Ctx *c, const ust_opts &op, int n)
     return UST_OK;
 }
 
+int ilog2_ceil(long long x)
+{
+    int l = 0;
+    while ((1ll << l) < x) ++l;
+    return l;
+}
+
+// The tuned launch shape of a single graph (ust_opts.autotune = 1): probes of
+// 2 x (most CTAs of any candidate) trees, at most 2,432.
+int tune_single(Ctx *c, int *bt, int *cps)
+{
+    int32_t rp2[2] = {0, 0};
+    UST_CUDA_TRY(cudaMemcpyAsync(rp2, c->d_rp + c->pivot, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    ust::TuneKey key;
+    key.kernel = c->n <= ust::kSmemMaxVertices ? 0 : c->n <= ust::kTierMaxVertices ? 1 : 2;
+    key.n_bucket = (c->n + 4095) / 4096;
+    key.avg_deg = (int)((int64_t)c->nnz / c->n);
+    key.pivot_deg_log2 = ilog2_ceil(std::max(1, rp2[1] - rp2[0]));
+    key.graphs_log2 = 0;
+    key.sms = c->num_sms;
+    int rc = ust::upload_single_desc(c);
+    if (rc) return rc;
+    const long long max_rounds =
+        c->max_pop_rounds > 0 ? c->max_pop_rounds
+                              : std::min<int64_t>(16ll * ((int64_t)c->nnz * std::max(1, c->ecc) + c->n) + 1024, 1ll << 30);
+    const long long items = 2ll * c->num_sms * 8;
+    ust::LaunchCfg best;
+    rc = ust::tune_launch(c, key, c->d_graphs, c->d_items, 1, items, c->n, max_rounds, c->d_Rtmp, &best, nullptr);
+    if (rc) return rc;
+    *bt = best.bt;
+    *cps = best.ctas / std::max(1, c->num_sms);
+    return UST_OK;
+}
+
 int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
 {
     const int n = g->n, nnz = g->nnz;
@@ -146,13 +187,32 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
         c->blocks = true;
         rc = ust::build_block_rows(c);
         if (rc) return rc;
+    } else if (n > ust::kTierMaxVertices) {  // the large-graph sampler's degree-ordered view
+        rc = ust::build_relabel(c);
+        if (rc) return rc;
+        rc = ust::relabel_paths(c);
+        if (rc) return rc;
     }
-    rc = ust::alloc_sampler(c, op.block_threads, op.ctas_per_sm);
+    int bt = op.block_threads, cps = op.ctas_per_sm;
+    if (op.autotune > 0 && bt == 0 && cps == 0 && !c->blocks) {
+        rc = tune_single(c, &bt, &cps);
+        if (rc) return rc;
+    }
+    rc = ust::alloc_sampler(c, bt, cps);
     if (rc) return rc;
     rc = ust::alloc_solver(c);
     if (rc) return rc;
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->ready = true;
     return UST_OK;
+}
+
+// Sampling calls need B_u, the sampler's paths and walk rows of the current
+// pivot: after a ust_reset that failed part-way they may not match.
+int check_ready(Ctx *c)
+{
+    if (c->batch || c->ready) return UST_OK;
+    return ust::fail(c, UST_ESTATE, "the last ust_reset failed: call ust_reset again before sampling");
 }
 
 // The sampler draws from the context's CSR pointers. With the
@@ -333,6 +393,7 @@ int ust_reset(ust_ctx *h, int32_t pivot)
         return ust::batch_reset(c);
     }
     if (pivot < 0 || pivot >= c->n) return ust::fail(c, UST_EINVAL, "pivot out of range");
+    c->ready = false;  // set again only once B_u, the paths and the walk rows all match the new pivot
     c->pivot = pivot;
     c->trees = 0;
     c->draws = 0;
@@ -342,9 +403,16 @@ int ust_reset(ust_ctx *h, int32_t pivot)
     c->x_valid = false;
     UST_CUDA_TRY(cudaMemsetAsync(c->d_R, 0, (size_t)c->n * 8, c->stream));
     if (c->d_ecount) UST_CUDA_TRY(cudaMemsetAsync(c->d_ecount, 0, (size_t)c->nnz * 8, c->stream));
-    const int rc = ust::run_bfs(c);
-    if (rc || !c->blocks) return rc;
-    return ust::build_block_rows(c);  // parent blocks follow the new B_u
+    int rc = ust::run_bfs(c);
+    if (rc) return rc;
+    rc = ust::relabel_paths(c);  // the large-graph sampler's paths follow the new B_u
+    if (rc) return rc;
+    if (c->blocks) {
+        rc = ust::build_block_rows(c);  // parent blocks follow the new B_u
+        if (rc) return rc;
+    }
+    c->ready = true;
+    return UST_OK;
 }
 
 int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
@@ -354,6 +422,7 @@ int ust_sample_aggregate(ust_ctx *h, int64_t n_trees, uint64_t seed)
     if (n_trees < 0) return ust::fail(c, UST_EINVAL, "n_trees < 0");
     if (n_trees == 0) return UST_OK;
     if (c->batch) return ust::batch_sample_aggregate(c, n_trees, seed);
+    if (const int rc = check_ready(c)) return rc;
     UST_CUDA_TRY(cudaMemcpyAsync(c->d_Rtmp, c->d_R, (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (c->d_ecount)
         UST_CUDA_TRY(cudaMemcpyAsync(c->d_ecount_tmp, c->d_ecount, (size_t)c->nnz * 8, cudaMemcpyDeviceToDevice,
@@ -522,6 +591,7 @@ int ust_tree_range_counts(ust_ctx *h, int64_t t0, int64_t t1, uint64_t seed, int
     Ctx *c = &h->c;
     if (!R_out || t0 < 0 || t1 < t0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
     if (c->batch) return ust::fail(c, UST_EINVAL, "ust_tree_range_counts applies to single-graph contexts");
+    if (const int rc = check_ready(c)) return rc;
     UST_CUDA_TRY(cudaMemsetAsync(c->d_Rtmp, 0, (size_t)c->n * 8, c->stream));
     int rc;
     {
@@ -555,6 +625,7 @@ int ust_sample_trees(ust_ctx *h, int64_t t0, int32_t count, uint64_t seed, int32
     Ctx *c = &h->c;
     if (!next_out || count < 0 || t0 < 0) return ust::fail(c, UST_EINVAL, "bad tree range or output");
     if (c->batch) return ust::fail(c, UST_EINVAL, "ust_sample_trees applies to single-graph contexts");
+    if (const int rc = check_ready(c)) return rc;
     if (count == 0) return UST_OK;
     const size_t elems = (size_t)count * (size_t)c->n;
     int32_t *d_next = nullptr, *d_pops = nullptr;

@@ -47,6 +47,8 @@ GraphDesc desc_of(const Ctx *c, int g, long long tree_begin)
     d.powner = c->d_path + 2 * c->path_cap + c->bpoff[g];
     d.fc = (int)c->bfarness[g];
     d.aoff = c->baoff[g];
+    d.orig = nullptr;
+    d.rp_in = nullptr;
     return d;
 }
 
@@ -86,6 +88,60 @@ int batch_prepare(Ctx *c, bool fill)
         if (st & 1) return fail(c, UST_ENOTCONNECTED, "graph " + std::to_string(g) + " is not connected");
         if (fill && (st & 2)) return fail(c, UST_ECUDA, "batch B_u: path space mismatch");
         c->becc[g] = c->h_prep_out[B + g];
+    }
+    return UST_OK;
+}
+
+// The tuned launch shape of every size class (ust_opts.autotune): each class
+// is probed with the same number of trees of each of its graphs, about
+// 2,432 work items in all, counts into the scratch row of R.
+int tune_batch_classes(Ctx *c, const std::vector<int32_t> &hrp)
+{
+    const int B = c->batch;
+    for (int k = 0; k < kNumClasses; ++k) {
+        std::vector<int> group;
+        for (int g = 0; g < B; ++g)
+            if (c->bclass[g] == k) group.push_back(g);
+        if (group.empty()) continue;
+        const int G = (int)group.size();
+        const long long target = 2ll * c->num_sms * 8;
+        const long long t = std::max<long long>(1, (target + G - 1) / G);
+        std::vector<GraphDesc> descs;
+        std::vector<long long> starts;
+        long long nsum = 0, asum = 0, max_rounds = 1024;
+        int pdeg = 1, maxn = 0;
+        for (int i = 0; i < G; ++i) {
+            const int g = group[i];
+            descs.push_back(desc_of(c, g, 0));
+            starts.push_back(t * i);
+            nsum += c->bn[g];
+            asum += c->bnnz[g];
+            maxn = std::max(maxn, c->bn[g]);
+            const int32_t *r = hrp.data() + c->bvoff[g] + g;
+            pdeg = std::max(pdeg, r[c->bpivot[g] + 1] - r[c->bpivot[g]]);
+            max_rounds = std::max<long long>(max_rounds,
+                                             16ll * ((long long)c->bnnz[g] * std::max(1, c->becc[g]) + c->bn[g]) + 1024);
+        }
+        if (c->max_pop_rounds > 0) max_rounds = c->max_pop_rounds;
+        starts.push_back(t * G);
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_graphs, descs.data(), descs.size() * sizeof(GraphDesc),
+                                     cudaMemcpyHostToDevice, c->stream));
+        UST_CUDA_TRY(cudaMemcpyAsync(c->d_items, starts.data(), starts.size() * sizeof(long long),
+                                     cudaMemcpyHostToDevice, c->stream));
+        TuneKey key;
+        key.kernel = maxn <= kSmemMaxVertices ? 0 : maxn <= kTierMaxVertices ? 1 : 2;
+        key.n_bucket = k;  // the class itself
+        key.avg_deg = (int)(asum / std::max<long long>(1, nsum));
+        int l = 0;
+        while ((1 << l) < pdeg) ++l;
+        key.pivot_deg_log2 = l;
+        l = 0;
+        while ((1 << l) < G) ++l;
+        key.graphs_log2 = l;
+        key.sms = c->num_sms;
+        const int rc = tune_launch(c, key, c->d_graphs, c->d_items, G, t * G, maxn, max_rounds, c->d_Rtmp,
+                                   &c->class_tuned[k], nullptr);
+        if (rc) return rc;
     }
     return UST_OK;
 }
@@ -304,6 +360,10 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
     c->ecc = *std::max_element(c->becc.begin(), c->becc.end());
     c->farness = c->bpoff[B];
 
+    if (op.autotune >= 0 && op.block_threads == 0 && op.ctas_per_sm == 0) {
+        rc = tune_batch_classes(c, hrp);
+        if (rc) return rc;
+    }
     rc = alloc_batch_sampler(c, op.block_threads, op.ctas_per_sm);
     if (rc) return rc;
 

@@ -266,20 +266,30 @@ __global__ void bt_pre_kernel(int n, int level, const int32_t *__restrict__ dist
     }
 }
 
+// The kernels that scan adjacency rows take one warp per row, lanes striding
+// the row, so that the rows of hubs do not serialise on one thread.
+__device__ __forceinline__ int warp_id_global() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int warps_global() { return (int)((gridDim.x * blockDim.x) >> 5); }
+
 __global__ void bt_local_kernel(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre, int32_t *lo,
                                 int32_t *hi)
 {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int v = warp_id_global(); v < n; v += warps_global()) {
         int l = pre[v], h = pre[v];
-        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+        for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
             const int w = ci[e];
             if (tree_edge(v, w, bpar)) continue;
             l = min(l, pre[w]);
             h = max(h, pre[w]);
         }
-        lo[v] = l;
-        hi[v] = h;
+        l = __reduce_min_sync(0xffffffffu, l);
+        h = __reduce_max_sync(0xffffffffu, h);
+        if (lane == 0) {
+            lo[v] = l;
+            hi[v] = h;
+        }
     }
 }
 
@@ -304,7 +314,9 @@ __device__ int uf_find(int32_t *uf, int x, int n, int *bad)
         if (p == x) return x;
         const int g = __ldcg(uf + p);
         if (g == p) return p;
-        uf[x] = g;  // x is no root: any ancestor is a valid parent
+        // path halving: x is no root, so any ancestor is a valid parent; an
+        // atomic store, since other threads read uf and CAS roots meanwhile
+        atomicExch(uf + x, g);
         x = g;
     }
     atomicExch(bad, 1);
@@ -331,9 +343,10 @@ __global__ void bt_rule1_kernel(int n, const int32_t *__restrict__ rp, const int
                                 const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
                                 const int32_t *__restrict__ nd, int32_t *uf, int *bad)
 {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int v = warp_id_global(); v < n; v += warps_global()) {
         const int pv = pre[v], end = pv + nd[v];
-        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+        for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
             const int w = ci[e];
             if (tree_edge(v, w, bpar)) continue;
             const int pw = pre[w];
@@ -372,32 +385,42 @@ __global__ void wk_count_kernel(int n, int u, const int32_t *__restrict__ rp, co
                                 const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
                                 const int32_t *__restrict__ lab, int32_t *wdeg)
 {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int c = 0;
+    const int lane = threadIdx.x & 31;
+    for (int v = warp_id_global(); v < n; v += warps_global()) {
+        unsigned c = 0;
         if (v != u) {
             const int pb = lab[v];
-            for (int e = rp[v]; e < rp[v + 1]; ++e) c += (block_of(v, ci[e], bpar, pre, lab) == pb);
+            for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) c += (block_of(v, ci[e], bpar, pre, lab) == pb);
         }
-        wdeg[v] = c;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) wdeg[v] = (int)c;
     }
 }
 
+// Order-preserving fill: the lanes keep 32 consecutive entries per step and
+// place the kept ones by a ballot prefix.
 __global__ void wk_fill_kernel(int n, int u, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                const int32_t *__restrict__ bpar, const int32_t *__restrict__ pre,
                                const int32_t *__restrict__ lab, const int32_t *__restrict__ wrp, int32_t *wci,
                                int32_t *wmap)
 {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int v = warp_id_global(); v < n; v += warps_global()) {
         if (v == u) continue;
         const int pb = lab[v];
         int o = wrp[v];
-        const int o1 = wrp[v + 1];
-        for (int e = rp[v]; e < rp[v + 1] && o < o1; ++e) {
-            const int w = ci[e];
-            if (block_of(v, w, bpar, pre, lab) != pb) continue;
-            wci[o] = w;
-            wmap[o] = e;
-            ++o;
+        const int o1 = wrp[v + 1], e1 = rp[v + 1];
+        for (int e0 = rp[v]; e0 < e1; e0 += 32) {  // uniform per warp
+            const int e = e0 + lane;
+            const int w = (e < e1) ? ci[e] : -1;
+            const bool keep = w >= 0 && block_of(v, w, bpar, pre, lab) == pb;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            const int at = o + __popc(m & ((1u << lane) - 1u));
+            if (keep && at < o1) {
+                wci[at] = w;
+                wmap[at] = e;
+            }
+            o += __popc(m);
         }
     }
 }
@@ -623,14 +646,17 @@ int build_block_rows(Ctx *c)
             cudaMalloc(&c->d_wmap, (size_t)c->nnz * 4) != cudaSuccess)
             return fail(c, UST_ENOMEM, "block-restricted rows");
     }
-    int32_t *s = nullptr;
-    if (cudaMalloc(&s, 6 * (size_t)n * 4) != cudaSuccess) return fail(c, UST_ENOMEM, "block labels");
+    if (!c->d_bscratch && cudaMalloc(&c->d_bscratch, 6 * (size_t)n * 4) != cudaSuccess)
+        return fail(c, UST_ENOMEM, "block labels");  // kept: a later ust_reset allocates nothing
+    int32_t *s = c->d_bscratch;
     int32_t *nd = s, *pre = s + n, *cur = s + 2 * (size_t)n, *lo = s + 3 * (size_t)n, *hi = s + 4 * (size_t)n,
             *uf = s + 5 * (size_t)n;
     int32_t *lab = cur, *wdeg = lo;  // cur and lo are free again by then
     int *d_bad = c->d_flag;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    // one warp per row in the row scans
+    const int wblocks = (int)std::min<int64_t>(((int64_t)n * 32 + threads - 1) / threads, (int64_t)c->num_sms * 16);
     cudaStream_t st = c->stream;
     int rc = UST_OK;
     int64_t launches = 0;
@@ -649,16 +675,16 @@ int build_block_rows(Ctx *c)
         bt_size_kernel<<<blocks, threads, 0, st>>>(n, level, c->d_dist, c->d_bpar, nd);
     for (int level = 1; level <= c->ecc; ++level, ++launches)
         bt_pre_kernel<<<blocks, threads, 0, st>>>(n, level, c->d_dist, c->d_bpar, nd, pre, cur);
-    bt_local_kernel<<<blocks, threads, 0, st>>>(n, c->d_rp, c->d_ci, c->d_bpar, pre, lo, hi);
+    bt_local_kernel<<<wblocks, threads, 0, st>>>(n, c->d_rp, c->d_ci, c->d_bpar, pre, lo, hi);
     ++launches;
     for (int level = c->ecc; level >= 1; --level, ++launches)
         bt_lohi_kernel<<<blocks, threads, 0, st>>>(n, level, c->d_dist, c->d_bpar, lo, hi);
-    bt_rule1_kernel<<<blocks, threads, 0, st>>>(n, c->d_rp, c->d_ci, c->d_bpar, pre, nd, uf, d_bad);
+    bt_rule1_kernel<<<wblocks, threads, 0, st>>>(n, c->d_rp, c->d_ci, c->d_bpar, pre, nd, uf, d_bad);
     bt_rule2_kernel<<<blocks, threads, 0, st>>>(n, u, c->d_bpar, pre, nd, lo, hi, uf, d_bad);
     bt_label_kernel<<<blocks, threads, 0, st>>>(n, uf, lab, d_bad);
-    wk_count_kernel<<<blocks, threads, 0, st>>>(n, u, c->d_rp, c->d_ci, c->d_bpar, pre, lab, wdeg);
+    wk_count_kernel<<<wblocks, threads, 0, st>>>(n, u, c->d_rp, c->d_ci, c->d_bpar, pre, lab, wdeg);
     path_offsets_kernel<<<1, kScanThreads, 0, st>>>(n, wdeg, c->d_wrp);
-    wk_fill_kernel<<<blocks, threads, 0, st>>>(n, u, c->d_rp, c->d_ci, c->d_bpar, pre, lab, c->d_wrp, c->d_wci,
+    wk_fill_kernel<<<wblocks, threads, 0, st>>>(n, u, c->d_rp, c->d_ci, c->d_bpar, pre, lab, c->d_wrp, c->d_wci,
                                                c->d_wmap);
     launches += 6;
     BT_TRY(cudaGetLastError());
@@ -681,7 +707,6 @@ done:
 #undef BT_TRY
     c->launches += launches;
     cudaStreamSynchronize(st);
-    cudaFree(s);
     return rc;
 }
 

@@ -41,6 +41,11 @@ struct GraphDesc {
     const int32_t *pchild, *powner;
     int fc;
     long long aoff;  // offset of the graph's arcs in batch-wide arc arrays
+    // Graphs relabelled for the large-graph sampler (single graphs above
+    // kTierMaxVertices): rp / ci / u / path are in sampler ids, orig[v] is
+    // the input id of sampler vertex v (Philox counters, pathptr, outputs)
+    // and rp_in the input row_ptr (arc counts). NULL: ids are input ids.
+    const int32_t *orig, *rp_in;
 };
 
 // Graphs of at most this many vertices run the sampler with its per-tree
@@ -56,6 +61,19 @@ constexpr int kTierMaxVertices = 0xFFFF;
 struct LaunchCfg {
     int bt = 0;
     int ctas = 0;
+};
+
+// Workload key of a tuned launch shape: which sampler kernel, the size of
+// the launch's largest graph, average degree and pivot degree, number of
+// graphs and SMs.
+struct TuneKey {
+    int kernel = 0, n_bucket = 0, avg_deg = 0, pivot_deg_log2 = 0, graphs_log2 = 0, sms = 0;
+    bool operator<(const TuneKey &o) const
+    {
+        const int a[6] = {kernel, n_bucket, avg_deg, pivot_deg_log2, graphs_log2, sms};
+        const int b[6] = {o.kernel, o.n_bucket, o.avg_deg, o.pivot_deg_log2, o.graphs_log2, o.sms};
+        return std::lexicographical_compare(a, a + 6, b, b + 6);
+    }
 };
 
 // One linear system of the one-CTA column solve (see ust_solve_cta.cu).
@@ -123,7 +141,25 @@ struct Ctx {
     // entry's arc in the input CSR
     bool blocks = false;
     int32_t *d_wrp = nullptr, *d_wci = nullptr, *d_wmap = nullptr;
+    int32_t *d_bscratch = nullptr;  // 6 n words for the block labels, allocated with the first rows
     int64_t wnnz = 0;
+    // false while B_u (and, with wilson_blocks, the walk rows and the
+    // sampler's paths) may not match the pivot: from the start of a
+    // ust_reset until it succeeds. Every sampling call refuses to run then.
+    bool ready = false;
+
+    // The large-graph sampler's view of a single graph above
+    // kTierMaxVertices vertices (plain Wilson): vertex ids relabelled so
+    // that the kLargeHotMax highest-degree vertices come first (by degree,
+    // then id) and the rest follow in input order; every row keeps its
+    // input order. B_u, the solve and all outputs stay in input ids.
+    bool relabel = false;
+    int32_t *d_srp = nullptr, *d_sci = nullptr;     // relabelled CSR
+    int32_t *d_orig = nullptr, *d_newid = nullptr;  // sampler id -> input id, and back
+    int32_t *d_spath = nullptr;                     // flattened BFS paths in sampler ids
+    int64_t spath_cap = 0;
+    int spivot = 0;                                 // the pivot's sampler id
+    std::vector<int32_t> h_newid;
 
     // sampling
     LaunchCfg cfg;                  // single graph: the sampler's launch shape
@@ -182,6 +218,7 @@ struct Ctx {
     std::vector<int> bclass;              // size class of every graph
     int class_maxn[kNumClasses] = {};     // largest graph of every class (0 = empty)
     LaunchCfg class_cfg[kNumClasses];     // launch shape of every class
+    LaunchCfg class_tuned[kNumClasses];   // the tuner's shape per class (bt 0: not tuned)
     std::vector<int> bn, bnnz, bpivot, becc, bheavy_n, bblocks;
     std::vector<int64_t> bvoff, baoff, bpoff, bhoff, btrees, bfarness;
     GraphDesc *d_graphs = nullptr;  // sampler descriptors (one for a single graph)
@@ -223,6 +260,14 @@ inline void phase_close(Ctx *c, int ph)
 
 // Host drivers (one per translation unit).
 int run_bfs(Ctx *c);
+// Vertices whose counter words the large-graph sampler keeps in shared
+// memory at most (1024 threads, one CTA per SM); the relabelling puts the
+// highest-degree vertices below this id.
+constexpr int kLargeHotMax = 28 * 1024;
+// The relabelled CSR of the large-graph sampler (ust_relabel.cu), built once
+// per context, and its flattened BFS paths, rebuilt with every B_u.
+int build_relabel(Ctx *c);
+int relabel_paths(Ctx *c);
 // The walk rows of the biconnected-component variant for the current B_u.
 int build_block_rows(Ctx *c);
 // Arc counts of the variant's walk rows, scattered to the input CSR's arcs.
@@ -238,6 +283,14 @@ int select_pivot(Ctx *c, int n, const int32_t *d_rp, const int32_t *d_ci, int sw
 int alloc_sampler(Ctx *c, int block_threads, int ctas_per_sm);
 // The same for every size class of a batch.
 int alloc_batch_sampler(Ctx *c, int block_threads, int ctas_per_sm);
+// The fastest launch shape for `items` work items of d_graphs / d_items
+// (graphs of at most max_n vertices), timed on a probe whose counts go to
+// d_scratch; cached per key for the process.
+int tune_launch(Ctx *c, const TuneKey &key, const GraphDesc *d_graphs, const long long *d_items, int ngraphs,
+                long long items, int max_n, long long max_rounds, int64_t *d_scratch, LaunchCfg *out,
+                double *best_ms_per_item);
+// Uploads the single graph's sampler descriptor and item starts when they changed.
+int upload_single_desc(Ctx *c);
 // mode 0: aggregate trees [t0, t1) into d_out (int64 n) - added, not assigned.
 // mode 1: export next/pops of trees [t0, t1) to device buffers.
 int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,

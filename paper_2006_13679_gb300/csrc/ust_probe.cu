@@ -48,9 +48,22 @@ __global__ void __launch_bounds__(256) probe_kernel(int32_t *a, uint32_t mask, i
             for (int k = 0; k < kInFlight; ++k) v[k] = __ldcg(a + idx[k]);
 #pragma unroll
             for (int k = 0; k < kInFlight; ++k) acc += v[k];
-        } else {
+        } else if (mode == 1) {
 #pragma unroll
             for (int k = 0; k < kInFlight; ++k) atomicAdd(a + idx[k], 1);
+        } else {
+            // blocks of 16 << (mode - 2) bytes at aligned random positions,
+            // read as 16-byte vectors
+            const int vecs = 1 << (mode - 2);
+            const uint32_t block_mask = ~(uint32_t)(4 * vecs - 1);
+#pragma unroll
+            for (int k = 0; k < kInFlight; ++k) {
+                const int4 *q = reinterpret_cast<const int4 *>(a + (idx[k] & block_mask));
+                for (int j = 0; j < vecs; ++j) {
+                    const int4 v = __ldcg(q + j);
+                    acc += v.x ^ v.w;
+                }
+            }
         }
     }
     if (acc == 0x7FFFFFFF) sink[tid & 1023] = acc;  // keeps the loads alive
@@ -61,7 +74,7 @@ __global__ void __launch_bounds__(256) probe_kernel(int32_t *a, uint32_t mask, i
 extern "C" int ust_probe_random_access(int64_t bytes, int32_t mode, int32_t reps, void *stream,
                                        double *accesses_per_s)
 {
-    if (!accesses_per_s || (mode != 0 && mode != 1) || reps < 1 || bytes < (1 << 20) || bytes > (1ll << 36))
+    if (!accesses_per_s || mode < 0 || mode > 4 || reps < 1 || bytes < (1 << 20) || bytes > (1ll << 36))
         return -1;
     // the largest power-of-two word count that fits `bytes`
     uint64_t words = 1;

@@ -33,6 +33,7 @@
 //     upwards above v. Counts go to the CTA's partial row Rp; a second kernel
 //     sums the partial rows into the int64 R exactly.
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "ust_common.cuh"
@@ -85,6 +86,7 @@ struct SampleParams {
     int32_t *next_out, *pops_out;  // mode 1: item i's tree at [i n, (i + 1) n)
     unsigned long long *edge_counts;  // when set: +1 per tree at every arc v -> parent(v) (index aoff + arc)
     unsigned long long *R_direct;   // when set, counts go to R_direct[voff + v] (batches)
+    int hot;  // large-graph sampler: vertices whose counter words sit in shared memory
 };
 
 // item_start[1] of a one-graph launch: its items end at total_items.
@@ -171,54 +173,151 @@ constexpr int kFlatDepth = 8;
 // (64 registers per thread at most).
 constexpr int kThreadsPerSm = 1024;
 
-// SM = true: the per-tree counters live in shared memory (n words, n < 2^16):
-// in-degrees as "total | remaining" 16-bit halves, then the popping rounds'
-// marks, then "pending children | size sum" 16-bit halves. SM = false: the
-// same counters in global memory, 32-bit halves of a 64-bit word.
-template <int BT, bool SM>
-__global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kernel(SampleParams p)
+// ---------------------------------------------------------------------------
+// Graphs above kTierMaxVertices vertices: the per-tree state lives in the
+// CTA's workspace, with the hottest counter words in shared memory.
+//
+// Per vertex v of the sampler's graph:
+//   NP(v)  high 32 bits: stack depth of the current top, then (after the
+//          sizes pass) v's offset inside its parent's interval; low 32 bits:
+//          the stack top, the tree parent at the end (-1 at u)
+//   CW(v)  by phase: (children | in-edges removed by peeling),
+//          (children | round mark), (pending children | summed sizes),
+//          (preorder number | summed sizes)
+// CW words of the vertices below p.hot sit in shared memory. A single graph
+// is relabelled for the sampler so that these are the vertices of largest
+// degree: a uniformly drawn neighbour, and so most random successor,
+// counter and ancestor accesses, lands on them (on R-MAT scale 22 the
+// 28,672 highest-degree vertices, 1.2% of them, take 55% of the first
+// draws). The relabelling keeps every row in the input order and every
+// draw keyed by the input id (gd.orig), so the trees are unchanged.
+//
+// Phases per tree (one CTA per tree, CTA barriers only):
+//  1. first draws, in-degrees into CW (high words);
+//  2. round 0: in-degree peeling; each step removes one in-edge of y with
+//     one atomic on CW[y] (low word) that also says whether y is now a leaf;
+//  3. the vertices left with in-edges lie on cycles: the first round list;
+//  4. popping rounds as in the shared-memory sampler, marks in the low words,
+//     children counts kept up to date in the high words;
+//  5. subtree sizes and offsets by last arrivers; every arrival is logged,
+//     so the log lists each vertex before its parent;
+//  6. preorder numbers top-down over the log in reverse: pre(x) = pre(parent)
+//     + offset(x); a vertex whose parent is not numbered yet is retried in a
+//     later pass (each pass numbers at least the shallowest one left);
+//  7. Algorithm 2 per vertex over its flattened BFS path; the first edge
+//     (bfs_parent(v), v) needs no interval (v lies in its own subtree, and
+//     never below its own tree child).
+struct LargeWords {
+    unsigned long long *s;  // shared: the words of vertices below hot
+    unsigned long long *g;  // global: CW of vertex v at g[2 v] (slots below hot unused)
+    int hot;
+    __device__ __forceinline__ unsigned long long *w(int v) const { return v < hot ? s + v : g + 2 * (long long)v; }
+    __device__ __forceinline__ uint32_t *lo(int v) const { return reinterpret_cast<uint32_t *>(w(v)); }
+    __device__ __forceinline__ uint32_t *hi(int v) const { return reinterpret_cast<uint32_t *>(w(v)) + 1; }
+};
+
+// Preorder phase: vertices per chunk (a packed shared word each), the tag
+// and link values of the high words, and the rounds a warp waits for the
+// parents of deferred vertices before leaving them to the next pass.
+constexpr int kPreChunk = 2048;
+// Algorithm 2 entries per vertex loaded together in the large-graph sampler.
+constexpr int kAlg2Chunk = 2;
+constexpr uint32_t kPreTag = 0x80000000u;      // high word of a vertex of the current chunk
+constexpr uint32_t kPreRoot = 0xFFFFFFFEu;     // link: the sum is the final number
+constexpr uint32_t kPreDeferred = 0xFFFFFFFFu; // link: the parent lies in a later chunk
+constexpr int kPreorderSpin = 512;
+
+// Input id of sampler vertex v (identity when the graph is not relabelled).
+__device__ __forceinline__ int orig_of(const GraphDesc &g, int v) { return g.orig ? __ldg(g.orig + v) : v; }
+
+// Stack entry k of sampler vertex x whose input id is o: the row is x's,
+// the Philox counter o's.
+__device__ __forceinline__ int stack_entry_of(const GraphDesc &g, uint32_t key0, uint32_t key1, int x, int o,
+                                              uint32_t k, uint32_t tree)
 {
-    extern __shared__ uint32_t s_dyn[];
+    const int b = __ldg(g.rp + x);
+    const int e = __ldg(g.rp + x + 1);
+    const unsigned long long r = philox_x64((uint32_t)o, k, tree, g.graph, key0, key1);
+    return __ldg(g.ci + b + (int)__umul64hi(r, (unsigned long long)(e - b)));
+}
+
+// Appends val for the lanes with flag set, at most cap entries in all (later
+// ones are dropped and counted, so an inconsistent state cannot write past
+// the array). All 32 lanes must call it.
+__device__ __forceinline__ void warp_append_capped(bool flag, int val, int32_t *q, int *cnt, int cap)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int i = base + __popc(m & ((1u << lane) - 1u));
+    if (flag && i < cap) q[i] = val;
+}
+
+// A vertex id read from the per-tree state or the graph, about to be used as
+// an index: outside [0, n) it means an inconsistent state. The first failing
+// check records its site in stats[6] and the status; the id becomes u, which
+// ends every walk and chain, so no access leaves the arrays.
+__device__ __forceinline__ int checked_vertex(int v, int n, int u, int site, const SampleParams &p)
+{
+    if ((unsigned)v < (unsigned)n) return v;
+    atomicCAS(p.stats + 6, 0ull, (unsigned long long)site);
+    atomicOr(p.status, kStatusBadState);
+    return u;
+}
+
+// The same for 64-bit values.
+__device__ __forceinline__ void warp_append_pair(bool flag, unsigned long long val, unsigned long long *q, int *cnt,
+                                                 int cap)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int i = base + __popc(m & ((1u << lane) - 1u));
+    if (flag && i < cap) q[i] = val;
+}
+
+template <int BT>
+__global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large_kernel(SampleParams p)
+{
+    extern __shared__ unsigned long long s_hot[];
     const int tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
-    int32_t *nxt = base;              // stack tops; the tree's parent array at the end
-    int32_t *pop = base + 1 * S_;     // stack depth of the current top
-    int32_t *mark = base + 2 * S_;    // in-degree (round 0), then kFinal / round stamp
-    int32_t *pos = base + 3 * S_;     // index of a redrawn vertex in the round's list
-    int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // redrawn vertices of this / next round
-    int32_t *Sx = base + 6 * S_;      // S(x) as an index into the round's list, -1 = reaches u
-    int32_t *J0 = base + 7 * S_;   // with base + 8 * S_: packed 64-bit words (queue, preorder)
-    int32_t *owner = J0, *wlen = base + 8 * S_;  // during the popping rounds (see below)
-    int32_t *L0 = base + 9 * S_;   // leaf queue of the peeling
-    // children bookkeeping: high word = children not yet finished (the
-    // children count while sampling), low word = summed subtree sizes
-    unsigned long long *P = reinterpret_cast<unsigned long long *>(base + 11 * S_);
-    int32_t *off = XA;  // the interval phase reuses the round list
-    int32_t *rmark = SM ? reinterpret_cast<int32_t *>(s_dyn) : mark;  // marks of the popping rounds
-    uint32_t *C = s_dyn;                                           // shared counters (SM only)
-    constexpr uint32_t kC16 = 1u << 16;
+    // one 16-byte record per vertex (arrays 0 to 3): NP(v) at NP[2 v], CW(v)
+    // at NP[2 v + 1], so that an atomic on a vertex's CW word and the read of
+    // its NP word touch the same 32-byte sector
+    unsigned long long *NP = reinterpret_cast<unsigned long long *>(base);
+    int32_t *NP32 = base;  // NP32[4 v]: stack top / tree parent; NP32[4 v + 1]: depth / offset
+    unsigned long long *CWg = NP + 1;
+    int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // round lists, then preorder retries
+    int32_t *pos = base + 6 * S_;    // index of a redrawn vertex in the round's list
+    int32_t *Sx = base + 7 * S_;     // S(x) as an index into the round's list, -1 = reaches u
+    int32_t *owner = base + 8 * S_;  // the walk of this round that passed a vertex
+    int32_t *wlen = base + 9 * S_;   // vertices a walk passed before it stopped
+    int32_t *ord = base + 10 * S_;   // arrivals of the sizes pass, in order
     int32_t *Rp = p.Rp + (long long)blockIdx.x * p.max_n;
     constexpr unsigned long long kChild = 1ull << 32;
 
     __shared__ long long s_tree;
-    __shared__ int s_cnt, s_err, s_abort, s_qn, s_qh, s_linked;
-    __shared__ unsigned long long s_root_sum;  // the root's children: summed subtree sizes
+    __shared__ int s_cnt, s_err, s_linked, s_qn, s_qh;
     __shared__ unsigned long long s_draws;
-    __shared__ unsigned long long cyc[8];  // clock64 per phase, kept by thread 0
+    __shared__ unsigned long long cyc[8];
     __shared__ long long tmark;
     if (tid < 8) cyc[tid] = 0ull;
-#define UST_PHASE(k)                                    \
-    do {                                                \
-        if (tid == 0) {                                 \
-            const long long _now = clock64();           \
+#define UST_PHASE(k)                                      \
+    do {                                                  \
+        if (tid == 0) {                                   \
+            const long long _now = clock64();             \
             cyc[k] += (unsigned long long)(_now - tmark); \
-            tmark = _now;                               \
-        }                                               \
+            tmark = _now;                                 \
+        }                                                 \
     } while (0)
 
     unsigned long long my_draws = 0, my_rounds = 0;
-
     int my_max_rounds = 0, my_max_pops = 0;
 
     for (;;) {
@@ -229,76 +328,64 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
         if (!item_graph(p, s_tree, gd, t)) break;
         const int n = gd.n, u = gd.u;
         const uint32_t tree = (uint32_t)t;
-        if (tid == 0) tmark = clock64();
-
-        // ---- 1. cycle popping --------------------------------------------
-        for (int v = tid; v < n; v += BT) {
-            pop[v] = 0;
-            if (SM) {
-                C[v] = 0u;
-            } else {
-                mark[v] = 0;
-                P[v] = 0ull;
-            }
-            nxt[v] = (v == u) ? -1 : stack_entry(gd, p.key0, p.key1, v, 0u, tree);
-        }
+        const LargeWords W{s_hot, CWg, min(p.hot, n)};
         if (tid == 0) {
+            tmark = clock64();
             s_draws = (unsigned long long)(n - 1);
             s_cnt = 0;
             s_err = 0;
-            s_abort = 0;
-            s_root_sum = 0ull;
+            s_qn = 0;
         }
+
+        // ---- 1. first draws and in-degrees ---------------------------------
+        for (int w = tid; w < W.hot; w += BT) s_hot[w] = 0ull;
+        for (int v = W.hot + tid; v < n; v += BT) CWg[2ll * v] = 0ull;
         __syncthreads();
-        UST_PHASE(0);
-        // in-degrees: mark is consumed by peeling, P keeps the children count
-        // (the root's counters are never needed and are left alone)
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int y[kWalks];
+            int o[kWalks], rb[kWalks], deg[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                y[k] = (v < n && v != u) ? nxt[v] : u;
+                const bool ok = v < n && v != u;
+                o[k] = ok ? orig_of(gd, v) : 0;
+                rb[k] = ok ? __ldg(gd.rp + v) : 0;
+                deg[k] = ok ? __ldg(gd.rp + v + 1) - rb[k] : 0;
+            }
+            int y[kWalks];
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const unsigned long long x = philox_x64((uint32_t)o[k], 0u, tree, gd.graph, p.key0, p.key1);
+                y[k] = (deg[k] > 0) ? __ldg(gd.ci + rb[k] + (int)__umul64hi(x, (unsigned long long)deg[k])) : -1;
             }
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
-                if (y[k] != u) {
-                    if (SM) {
-                        atomicAdd(&C[y[k]], kC16 + 1u);  // total and remaining in-degree
-                    } else {
-                        atomicAdd(&mark[y[k]], 1);
-                        atomicAdd(&P[y[k]], kChild);
-                    }
+                const int v = b0 + k * BT;
+                if (v < n) {
+                    NP[2ll * v] = (unsigned long long)(uint32_t)y[k];
+                    if (y[k] >= 0 && y[k] != u) atomicAdd(W.w(checked_vertex(y[k], n, u, 1, p)), kChild);  // u's counters are never needed
                 }
             }
         }
         __syncthreads();
-        UST_PHASE(1);
-        // round 0: peel from the leaves; a thread that removes a vertex's
-        // last in-edge continues with that vertex. What is left are the
-        // vertices on cycles. The successors of the leaves are queued first;
-        // every thread keeps kWalks walks in flight and refills a finished
-        // walk from the queue (one entry prefetched). Each step removes the
-        // in-edge of y and fetches y's successor in the same round trip.
+        UST_PHASE(0);
+
+        // ---- 2. round 0: in-degree peeling -----------------------------------
+        // Every thread starts walks at its own leaves (no children) and keeps
+        // kWalks in flight; a step adds 1 to y's removed in-edges and, when
+        // that was y's last one, continues with y's successor.
         {
-            int32_t *Q = L0;  // free until the popping rounds
-            if (tid == 0) {
-                s_qn = 0;
-                s_qh = 0;
+            // the leaves' successors first, in one coalesced sweep (the log
+            // array is free until the sizes pass); walks then take them from
+            // this queue, one prefetched ahead
+            int32_t *Q = ord;
+            if (tid == 0) s_qh = 0;
+            for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
+                const bool leaf = v < n && v != u && (*W.w(v) >> 32) == 0ull;
+                const int y0 = leaf ? checked_vertex(NP32[4ll * v], n, u, 2, p) : u;
+                warp_append_capped(leaf && y0 != u, y0, Q, &s_qn, n);
             }
             __syncthreads();
-            const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
-            for (int it = 0; it < iters; ++it) {
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int v = tid + (it * kWalks + k) * BT;
-                    const bool leaf = v < n && v != u && (SM ? (C[v] >> 16) == 0u : (P[v] >> 32) == 0ull);
-                    const int y0 = leaf ? nxt[v] : u;
-                    warp_append(leaf && y0 != u, y0, Q, &s_qn);
-                }
-            }
-            __syncthreads();
-            const int qn = s_qn;
+            const int qn = min(s_qn, n);
             int idx = atomicAdd(&s_qh, 1);
             int spare = (idx < qn) ? Q[idx] : u;
             int y[kWalks];
@@ -308,20 +395,23 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
                 idx = (spare != u) ? atomicAdd(&s_qh, 1) : qn;
                 spare = (idx < qn) ? Q[idx] : u;
             }
+            bool done = false;
             for (int guard = 0; guard <= 2 * n + 2; ++guard) {
-                int old[kWalks], ny[kWalks];
+                unsigned long long old[kWalks];
+                int ny[kWalks];
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    if (SM)
-                        old[k] = (y[k] != u) ? (int)(atomicSub(&C[y[k]], 1u) & 0xFFFFu) : 0;
-                    else
-                        old[k] = (y[k] != u) ? atomicSub(&mark[y[k]], 1) : 0;
-                    ny[k] = (y[k] != u) ? nxt[y[k]] : u;
+                    old[k] = 0ull;
+                    ny[k] = u;
+                    if (y[k] != u) {
+                        old[k] = atomicAdd(W.w(y[k]), 1ull);
+                        ny[k] = checked_vertex(NP32[4ll * y[k]], n, u, 3, p);
+                    }
                 }
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
-                    if (y[k] != u && old[k] == 1) {
+                    if (y[k] != u && (uint32_t)old[k] + 1u == (uint32_t)(old[k] >> 32)) {
                         y[k] = ny[k];  // y peeled: remove its out-edge next
                     } else {
                         y[k] = spare;
@@ -330,34 +420,40 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
                     }
                     any |= (y[k] != u);
                 }
-                if (!any) break;
+                if (!any) {
+                    done = true;
+                    break;
+                }
             }
+            if (!done) s_err = 1;
         }
         __syncthreads();
-        if (!SM && tid == 0) mark[u] = kFinal;
-        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int m[kWalks];
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                m[k] = (v < n && v != u) ? (SM ? (int)(C[v] & 0xFFFFu) : mark[v]) : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k)
-                if (m[k] > 0) XA[atomicAdd(&s_cnt, 1)] = b0 + k * BT;  // cycle vertices
-        }
-        __syncthreads();
-        if (SM) {  // the shared words now hold the rounds' marks
-            for (int v = tid; v < n; v += BT) rmark[v] = (v == u) ? kFinal : 0;
-            __syncthreads();
-        }
-        UST_PHASE(2);
-        int nX = s_cnt;
+        UST_PHASE(1);
 
+        // ---- 3. the first round list: vertices with in-edges left ------------
+        for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
+            bool on_cycle = false;
+            if (v < n) {
+                const unsigned long long w = *W.w(v);
+                if (v == u) {
+                    *W.lo(v) = (uint32_t)kFinal;
+                } else {
+                    on_cycle = (uint32_t)w < (uint32_t)(w >> 32);
+                    if ((uint32_t)w != 0u) *W.lo(v) = 0u;  // the low words become round marks
+                }
+            }
+            warp_append_capped(on_cycle, v, XA, &s_cnt, n);
+        }
+        __syncthreads();
+        UST_PHASE(2);
+        int nX = min(s_cnt, n);
+
+        // ---- 4. popping rounds -------------------------------------------------
         int rounds = 0;
-        bool failed = false;
+        bool failed = s_err != 0;
+        if (failed && tid == 0) atomicOr(p.status, kStatusBadState);
         int32_t *X = XA, *Xn = XB;
-        while (nX > 0) {
+        while (!failed && nX > 0) {
             ++rounds;
             if (rounds > p.max_rounds) {
                 failed = true;
@@ -366,18 +462,17 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
             }
             // (a) pop: every vertex on a cycle advances to its next stack entry
             for (int i = tid; i < nX; i += BT) {
-                const int x = X[i];
-                const int k = pop[x] + 1;
-                const int old = nxt[x];
-                const int y = stack_entry(gd, p.key0, p.key1, x, (uint32_t)k, tree);
-                pop[x] = k;
-                nxt[x] = y;
-                rmark[x] = rounds;
+                const int x = checked_vertex(X[i], n, u, 4, p);
+                if (x == u) continue;
+                const unsigned long long wx = NP[2ll * x];
+                const uint32_t k = (uint32_t)(wx >> 32) + 1u;
+                const int old = checked_vertex((int)(uint32_t)wx, n, u, 5, p);
+                const int y = checked_vertex(stack_entry_of(gd, p.key0, p.key1, x, orig_of(gd, x), k, tree), n, u, 5, p);
+                NP[2ll * x] = ((unsigned long long)k << 32) | (uint32_t)y;
+                *W.lo(x) = (uint32_t)rounds;
                 pos[x] = i;
-                if (!SM) {
-                    if (old != u) atomicAdd(&P[old], 0ull - kChild);
-                    if (y != u) atomicAdd(&P[y], kChild);
-                }
+                if (old != u) atomicAdd(W.hi(old), 0xFFFFFFFFu);  // one child less
+                if (y != u) atomicAdd(W.hi(y), 1u);
             }
             if (tid == 0) {
                 s_draws += (unsigned long long)nX;
@@ -386,35 +481,41 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
                 my_max_pops = max(my_max_pops, nX);
             }
             __syncthreads();
-            // (b) S(x): first redrawn vertex or known-final vertex after x;
-            //     a walk that reaches a vertex another walk of this round
-            //     passed (mark -2 - rounds) stops and takes that walk's
-            //     result, resolved after the barrier (as in the
-            //     shared-memory kernel)
+            // (b) S(x): the first redrawn or known-final vertex after x; a walk
+            //     that reaches a vertex another walk of this round passed
+            //     stops and takes that walk's result (owner published before
+            //     the mark, block fence), resolved after the barrier
             const int vis = -2 - rounds;
             for (int i = tid; i < nX; i += BT) {
-                int y = nxt[X[i]];
+                int y = checked_vertex(NP32[4ll * checked_vertex(X[i], n, u, 6, p)], n, u, 6, p);
                 int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
-                    const int m = rmark[y];
-                    const int ny = nxt[y];
-                    if (m == kFinal) { res = -1; break; }
-                    if (m == rounds) { res = pos[y]; break; }
+                    const int m = (int)*W.lo(y);
+                    const int ny = NP32[4ll * y];  // checked below, before it is used
+                    if (m == kFinal) {
+                        res = -1;
+                        break;
+                    }
+                    if (m == rounds) {
+                        res = pos[y];
+                        break;
+                    }
                     if (m == vis) {
                         __threadfence_block();
                         res = -3 - owner[y];
                         s_linked = 1;
                         break;
                     }
-                    if (len >= kQuietSteps) {  // short walks skip the bookkeeping
-                        owner[y] = i;
-                        __threadfence_block();  // the owner is visible before the mark
-                        rmark[y] = vis;
-                    }
+                    owner[y] = i;
+                    __threadfence_block();  // the owner is visible before the mark
+                    *W.lo(y) = (uint32_t)vis;
                     ++len;
-                    y = ny;
+                    y = checked_vertex(ny, n, u, 7, p);
                 }
-                if (res == -2) { s_err = 1; res = -1; }
+                if (res == -2) {
+                    s_err = 1;
+                    res = -1;
+                }
                 Sx[i] = res;
                 wlen[i] = len;
             }
@@ -427,36 +528,40 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
                         if (j >= nX) break;  // not a walk of this round: reported below
                         r = Sx[j];
                     }
-                    if (r <= -3 || r >= nX) { s_err = 1; r = -1; }
-                    Sx[i] = r;
+                    if (r <= -3 || r >= nX) {
+                        s_err = 1;
+                        r = -1;
+                    }
+                    Sx[i] = r;  // a reader sees the link or its result: both lead to the same end
                 }
                 __syncthreads();
             }
-            // (c) nodes that reach -1 mark x and their own walked part final;
-            //     nodes on a cycle of i -> S(i) queue their whole segment for
-            //     popping
+            // (c) nodes that reach -1 mark x and their walked part final; nodes
+            //     on a cycle of i -> S(i) queue their whole segment for popping
             for (int i = tid; i < nX; i += BT) {
                 const int kind = classify_node(Sx, i, nX);
-                int y = X[i];
+                int y = checked_vertex(X[i], n, u, 8, p);
                 if (kind == 1) {
                     const int len = wlen[i];
-                    rmark[y] = kFinal;
+                    *W.lo(y) = (uint32_t)kFinal;
                     for (int k = 0; k < len; ++k) {
-                        y = nxt[y];
-                        rmark[y] = kFinal;
+                        y = checked_vertex(NP32[4ll * y], n, u, 8, p);
+                        *W.lo(y) = (uint32_t)kFinal;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
                         Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
-                        y = max(nxt[y], 0);  // nxt[u] = -1: an inconsistent walk stays in the array
-                        if (rmark[y] == rounds) break;
+                        y = checked_vertex(max(NP32[4ll * y], 0), n, u, 8, p);  // -1 at u: an inconsistent walk stays in the arrays
+                        if ((int)*W.lo(y) == rounds) break;
                     }
-                    if (rmark[y] != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
+                    if ((int)*W.lo(y) != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
                 }
             }
             __syncthreads();
             nX = s_cnt;
-            int32_t *tmp = X; X = Xn; Xn = tmp;
+            int32_t *tmp = X;
+            X = Xn;
+            Xn = tmp;
             if (s_err || nX > n) {
                 failed = true;
                 if (tid == 0) atomicOr(p.status, kStatusBadState);
@@ -474,292 +579,326 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
         if (p.edge_counts) {  // the tree's arcs v -> parent(v): the final stack entry of every v
             for (int v = tid; v < n; v += BT) {
                 if (v == u) continue;
+                const int o = orig_of(gd, v);
                 const int b = __ldg(gd.rp + v), e = __ldg(gd.rp + v + 1);
-                const unsigned long long x = philox_x64((uint32_t)v, (uint32_t)pop[v], tree, gd.graph, p.key0, p.key1);
-                atomicAdd(p.edge_counts + gd.aoff + b + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
+                const uint32_t k = (uint32_t)(NP[2ll * v] >> 32);
+                const unsigned long long x = philox_x64((uint32_t)o, k, tree, gd.graph, p.key0, p.key1);
+                const long long row = gd.rp_in ? (long long)__ldg(gd.rp_in + o) : (long long)b;  // input arc index
+                atomicAdd(p.edge_counts + gd.aoff + row + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
             }
         }
-
-        if (p.mode == 1) {
-            const long long o = s_tree * (long long)n;
+        if (p.mode == 1) {  // export the tree in input ids
+            const long long ob = s_tree * (long long)n;
             for (int v = tid; v < n; v += BT) {
-                p.next_out[o + v] = nxt[v];
-                if (p.pops_out) p.pops_out[o + v] = pop[v];
+                const unsigned long long w = NP[2ll * v];
+                const int o = orig_of(gd, v);
+                const int tp = (int)(uint32_t)w;
+                p.next_out[ob + o] = (tp < 0) ? -1 : orig_of(gd, tp);
+                if (p.pops_out) p.pops_out[ob + o] = (int)(w >> 32);
             }
             __syncthreads();
             continue;
         }
+        // the low words sum subtree sizes from now on
+        for (int v = tid; v < n; v += BT)
+            if (*W.lo(v) != 0u) *W.lo(v) = 0u;
+        if (tid == 0) {
+            s_qn = 0;  // arrivals logged
+            s_cnt = 0; // leaves queued
+            s_qh = 0;
+        }
         __syncthreads();
 
-        // ---- 2. DFS intervals ---------------------------------------------
-        if (SM) {  // the shared words now count children and sum their sizes
-            for (int v = tid; v < n; v += BT) C[v] = 0u;
-            __syncthreads();
-            for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-                int y[kWalks];
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int v = b0 + k * BT;
-                    y[k] = (v < n && v != u) ? nxt[v] : -1;
-                }
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k)
-                    if (y[k] >= 0) atomicAdd(&C[y[k]], kC16);
-            }
-            __syncthreads();
-        }
-        // Subtree sizes from the leaves (P[v] == 0 exactly for leaves: an
-        // inner vertex always has pending children or a nonzero size sum).
-        // A child arriving at its parent gets, from the same atomic, the sizes
-        // of the siblings that arrived before it: its offset inside the
-        // parent's interval. Each step issues the atomic at the parent and the
-        // load of the parent's parent together. The root's sum lives in shared
-        // memory.
+        // ---- 5. subtree sizes and offsets ---------------------------------------
+        // A leaf's word is 0 (no children, nothing summed); an inner vertex's
+        // never is (children pending, or a size summed). An arrival of x at
+        // its parent adds x's size and removes one pending child in one
+        // atomic, whose old value gives x's offset; the last arriver carries
+        // the parent's size upwards. Arrivals are logged before their atomic.
         {
-            unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(J0);  // (leaf, parent) pairs
-            if (tid == 0) {
-                s_qn = 0;
-                s_qh = 0;
+            // (leaf, parent) pairs first, in one coalesced sweep, into the
+            // round lists' space (XA and XB as one 64-bit array); chains then
+            // take them from this queue, one prefetched ahead
+            unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(XA);
+            for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
+                const bool leaf = v < n && v != u && *W.w(v) == 0ull;
+                const int pv = leaf ? checked_vertex(NP32[4ll * v], n, u, 9, p) : u;
+                warp_append_pair(leaf, ((unsigned long long)(uint32_t)v << 32) | (uint32_t)pv, Q2, &s_cnt, n);
             }
             __syncthreads();
-            const int iters = (n + BT * kWalks - 1) / (BT * kWalks);
-            for (int it = 0; it < iters; ++it) {
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int v = tid + (it * kWalks + k) * BT;
-                    const bool leaf = v < n && v != u && (SM ? C[v] == 0u : P[v] == 0ull);
-                    const unsigned m = __ballot_sync(0xffffffffu, leaf);
-                    const unsigned lane = threadIdx.x & 31u;
-                    int b = 0;
-                    if (lane == 0 && m) b = atomicAdd(&s_qn, __popc(m));
-                    b = __shfl_sync(0xffffffffu, b, 0);
-                    if (leaf)
-                        Q2[b + __popc(m & ((1u << lane) - 1u))] =
-                            ((unsigned long long)(uint32_t)v << 32) | (uint32_t)nxt[v];
-                }
-            }
-            __syncthreads();
-            const int qn = s_qn;
-            const unsigned long long kNone = ~0ull;
+            const int qn = min(s_cnt, n);
+            constexpr unsigned long long kNone = ~0ull;
             int idx = atomicAdd(&s_qh, 1);
             unsigned long long spare = (idx < qn) ? Q2[idx] : kNone;
             int x[kWalks], par[kWalks];
-            unsigned long long carry[kWalks];
+            uint32_t carry[kWalks];
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
                 par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
-                carry[k] = 1ull;
+                carry[k] = 1u;
                 idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
                 spare = (idx < qn) ? Q2[idx] : kNone;
             }
+            bool done = false;
             for (int guard = 0; guard <= 2 * n + 2; ++guard) {
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) warp_append_capped(par[k] >= 0, x[k], ord, &s_qn, n);
                 unsigned long long old[kWalks];
                 int gp[kWalks];
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     old[k] = 0ull;
                     gp[k] = -1;
-                    if (SM) {
-                        // repack the 16|16 word as 32|32 so the code below is shared
-                        if (par[k] >= 0) {
-                            const uint32_t o = atomicAdd(&C[par[k]], (uint32_t)carry[k] - kC16);
-                            old[k] = ((unsigned long long)(o >> 16) << 32) | (o & 0xFFFFu);
-                            if (par[k] != u) gp[k] = nxt[par[k]];
-                        }
-                    } else if (par[k] == u) {
-                        old[k] = atomicAdd(&s_root_sum, carry[k]);
-                    } else if (par[k] >= 0) {
-                        old[k] = atomicAdd(&P[par[k]], carry[k] - kChild);
-                        gp[k] = nxt[par[k]];
+                    if (par[k] >= 0) {
+                        old[k] = atomicAdd(W.w(par[k]), (unsigned long long)carry[k] - kChild);
+                        if (par[k] != u) gp[k] = checked_vertex(NP32[4ll * par[k]], n, u, 10, p);
                     }
                 }
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     if (par[k] >= 0) {
-                        off[x[k]] = 1 + (int)(old[k] & 0xFFFFFFFFull);
-                        if (par[k] != u && (old[k] >> 32) == 1ull) {
-                            carry[k] = (old[k] & 0xFFFFFFFFull) + carry[k] + 1ull;
+                        NP32[4ll * x[k] + 1] = 1 + (int)(uint32_t)old[k];  // x's offset inside its parent's interval
+                        if (par[k] != u && (old[k] >> 32) == 1ull) {    // the last child: carry the size upwards
+                            carry[k] = (uint32_t)old[k] + carry[k] + 1u;
                             x[k] = par[k];
                             par[k] = gp[k];
                         } else {
                             x[k] = (spare != kNone) ? (int)(spare >> 32) : -1;
                             par[k] = (spare != kNone) ? (int)(uint32_t)spare : -1;
-                            carry[k] = 1ull;
+                            carry[k] = 1u;
                             idx = (spare != kNone) ? atomicAdd(&s_qh, 1) : qn;
                             spare = (idx < qn) ? Q2[idx] : kNone;
                         }
                     }
                     any |= (par[k] >= 0);
                 }
-                if (!any) break;
+                if (!__any_sync(0xffffffffu, any)) {
+                    done = true;
+                    break;
+                }
             }
+            if (!done) s_err = 1;
         }
         __syncthreads();
+        if (s_err || s_qn != n - 1) {  // every vertex but u arrives exactly once
+            if (tid == 0) atomicOr(p.status, kStatusBadState);
+            break;
+        }
         UST_PHASE(4);
-        // preorder numbers: pre[v] = sum of the offsets on the path from v up
-        // to u, by pointer jumping on packed (ancestor, partial sum) words.
-        // Updates are in place: a word read while its owner rewrites it is
-        // either the old or the new consistent pair, both valid.
-        unsigned long long *JA = reinterpret_cast<unsigned long long *>(J0);  // J0, J1
-        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-            int pa[kWalks], of[kWalks];
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                const bool ok = v < n && v != u;
-                pa[k] = ok ? nxt[v] : u;
-                of[k] = ok ? off[v] : 0;
+
+        // ---- 6. preorder numbers, top-down ---------------------------------------
+        // pre(u) = 0 and pre(x) = pre(parent) + offset(x) >= 1, written into
+        // the high word (0 after the sizes pass: no child pending). The log
+        // read backwards lists parents before their children; it is taken in
+        // chunks of kPreChunk vertices. A chunk's vertices are first tagged
+        // (high word = kPreTag | position in the chunk); then each one finds
+        // its parent numbered (an earlier chunk, or u), tagged (this chunk:
+        // a link), or neither (a later chunk, which the log order makes rare:
+        // deferred). Links are resolved by pointer jumping on packed
+        // (link, sum) words in shared memory, and the numbers written back.
+        // Deferred vertices are numbered afterwards in passes in which each
+        // warp waits a bounded number of rounds for the parents; what is
+        // still pending goes to the next pass.
+        {
+            unsigned long long *s_chunk = s_hot + min(p.hot, p.max_n);  // kPreChunk packed words
+            const int total = n - 1;
+            if (tid == 0) s_cnt = 0;  // deferred vertices, listed in XA
+            __syncthreads();
+            for (int c0 = 0; c0 < total; c0 += kPreChunk) {
+                const int len = min(kPreChunk, total - c0);
+                for (int i = tid; i < len; i += BT) {
+                    const int x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
+                    *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = kPreTag | (uint32_t)i;
+                }
+                __syncthreads();
+                for (int i = tid; i < len; i += BT) {
+                    const int x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
+                    const unsigned long long w = NP[2ll * x];
+                    const int par = checked_vertex((int)(uint32_t)w, n, u, 13, p);
+                    const uint32_t off = (uint32_t)(w >> 32);
+                    uint32_t link = kPreRoot, sum = off;
+                    if (par != u) {
+                        const uint32_t h = *reinterpret_cast<volatile uint32_t *>(W.hi(par));
+                        if (h & kPreTag)
+                            link = h & ~kPreTag;  // the parent is in this chunk
+                        else if (h != 0u)
+                            sum = h + off;  // numbered in an earlier chunk
+                        else
+                            link = kPreDeferred;
+                    }
+                    s_chunk[i] = ((unsigned long long)link << 32) | sum;
+                }
+                __syncthreads();
+                // pointer jumping: a word read while its owner rewrites it is
+                // the old or the new (link, sum) pair, and both are valid
+                for (int step = 0;; ++step) {
+                    bool any = false;
+                    if (step <= 32) {
+                        for (int i = tid; i < len; i += BT) {
+                            const unsigned long long a = s_chunk[i];
+                            const uint32_t l = (uint32_t)(a >> 32);
+                            if (l >= kPreRoot) continue;  // resolved or deferred
+                            const unsigned long long b = s_chunk[l];
+                            const uint32_t l2 = (uint32_t)(b >> 32);
+                            s_chunk[i] = l2 == kPreDeferred ? ((unsigned long long)kPreDeferred << 32)
+                                                            : ((unsigned long long)l2 << 32) |
+                                                                  (uint32_t)((uint32_t)a + (uint32_t)b);
+                            any = true;
+                        }
+                    }
+                    if (!__syncthreads_or(any)) break;
+                    if (step > 32) {  // a chunk of at most 2^32 entries resolves in 32 steps
+                        s_err = 1;
+                        break;
+                    }
+                }
+                for (int i = tid; i - (tid & 31) < len; i += BT) {  // uniform per warp
+                    bool deferred = false;
+                    int x = -1;
+                    if (i < len) {
+                        x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
+                        const unsigned long long a = s_chunk[i];
+                        deferred = (uint32_t)(a >> 32) != kPreRoot;
+                        *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = deferred ? 0u : (uint32_t)a;
+                    }
+                    warp_append_capped(deferred, x, XA, &s_cnt, n);
+                }
+                __syncthreads();
             }
-#pragma unroll
-            for (int k = 0; k < kWalks; ++k) {
-                const int v = b0 + k * BT;
-                if (v < n) JA[v] = ((unsigned long long)(uint32_t)pa[k] << 32) | (uint32_t)of[k];
+            int cnt = min(s_cnt, n);
+            int32_t *list = XA, *retry = XB;
+            for (int pass = 0; cnt > 0; ++pass) {
+                if (pass > n) {
+                    s_err = 1;
+                    break;
+                }
+                __syncthreads();
+                if (tid == 0) s_cnt = 0;
+                __syncthreads();
+                for (int b0 = tid; b0 - (tid & 31) < cnt; b0 += BT) {  // uniform per warp
+                    const int x = (b0 < cnt) ? checked_vertex(list[b0], n, u, 11, p) : -1;
+                    const unsigned long long w = (x >= 0) ? NP[2ll * x] : 0ull;
+                    const int par = (x >= 0) ? checked_vertex((int)(uint32_t)w, n, u, 13, p) : u;
+                    uint32_t pp = 0u;
+                    bool ok = x < 0 || par == u, written = x < 0;
+                    // the warp waits together, so a parent numbered by another
+                    // lane is seen one round later
+                    for (int spin = 0;; ++spin) {
+                        if (!ok) {
+                            pp = *reinterpret_cast<volatile uint32_t *>(W.hi(par));
+                            ok = pp != 0u;
+                        }
+                        if (ok && !written) {
+                            *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = pp + (uint32_t)(w >> 32);
+                            written = true;
+                        }
+                        if (__all_sync(0xffffffffu, written) || spin >= kPreorderSpin) break;
+                    }
+                    warp_append_capped(!written, x, retry, &s_cnt, n);
+                }
+                __syncthreads();
+                cnt = min(s_cnt, n);
+                int32_t *tmp = list;
+                list = retry;
+                retry = tmp;
             }
         }
         __syncthreads();
-        for (int step = 0; step < p.max_steps + 2; ++step) {
-            int pending = 0;
-            for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
-                unsigned long long a[kWalks], b[kWalks];
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int v = b0 + k * BT;
-                    a[k] = (v < n) ? JA[v] : ((unsigned long long)(uint32_t)u << 32);
-                }
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int j = (int)(a[k] >> 32);
-                    b[k] = (j != u) ? JA[j] : 0ull;
-                }
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) {
-                    const int j = (int)(a[k] >> 32);
-                    if (j == u) continue;
-                    const uint32_t j2 = (uint32_t)(b[k] >> 32);
-                    const uint32_t sum = (uint32_t)a[k] + (uint32_t)b[k];
-                    JA[b0 + k * BT] = ((unsigned long long)j2 << 32) | sum;
-                    pending |= ((int)j2 != u);
-                }
-            }
-            if (!__syncthreads_or(pending)) break;
-            if (step == p.max_steps + 1) s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) {
-            if (tid == 0) atomicOr(p.status, kStatusJumpSteps);
+        if (s_err) {
+            if (tid == 0) atomicOr(p.status, kStatusBadState);
             break;
         }
         UST_PHASE(5);
 
-        // ---- 3. Algorithm 2 ------------------------------------------------
-        // Shallow BFS paths (f^c(u) <= kFlatDepth n): one independent test per
-        // path entry, updates of R by atomics. Deep paths: one thread per
-        // vertex walks its own path and adds its count once.
-        if (gd.fc <= kFlatDepth * n) {
-            // One independent test per entry q of the flattened paths: the edge
-            // (a, b) = (path[q], pchild[q]) of P(v), v = powner[q]. The tree
-            // uses it downwards (parent(b) = a: +1 when v lies in b's subtree) or
-            // upwards (parent(a) = b: -1 when v lies in a's subtree).
-            for (int q0 = tid; q0 - (tid & 31) < gd.fc; q0 += BT * kPairs) {  // uniform per warp
-                int a[kPairs], b[kPairs], v[kPairs];
-    #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    const int q = q0 + k * BT;
-                    const bool ok = q < gd.fc;
-                    a[k] = ok ? __ldg(gd.path + q) : -1;
-                    b[k] = ok ? __ldg(gd.pchild + q) : 0;
-                    v[k] = ok ? __ldg(gd.powner + q) : 0;
-                }
-                int na[kPairs], nb[kPairs], tx[kPairs], sg[kPairs];
-    #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    na[k] = (a[k] >= 0) ? nxt[a[k]] : -2;
-                    nb[k] = (a[k] >= 0) ? nxt[b[k]] : -2;
-                }
-    #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    tx[k] = 0;
-                    sg[k] = 0;
-                    if (a[k] >= 0) {
-                        if (nb[k] == a[k]) {
-                            tx[k] = b[k];
-                            sg[k] = 1;
-                        } else if (na[k] == b[k]) {
-                            tx[k] = a[k];
-                            sg[k] = -1;
+        // ---- 7. Algorithm 2 ------------------------------------------------------
+        // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u (input order at
+        // pathptr[o], o = v's input id; entries in sampler ids). Edge (a_j+1,
+        // a_j) counts +1 when T uses it downwards (parent(a_j) = a_j+1) and v
+        // lies in a_j's subtree, -1 when T uses it upwards and v lies in
+        // a_j+1's subtree.
+        for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
+            int s0[kWalks], d[kWalks], prev[kWalks], nprev[kWalks], cnt[kWalks];
+            uint32_t pv[kWalks];
+            int dmax = 0;
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                const bool ok = v < n && v != u;
+                const int o = ok ? orig_of(gd, v) : 0;
+                s0[k] = ok ? __ldg(gd.pathptr + o) : 0;
+                d[k] = ok ? __ldg(gd.pathptr + o + 1) - s0[k] : 0;
+                prev[k] = v;
+                nprev[k] = ok ? NP32[4ll * v] : -2;
+                pv[k] = ok ? *W.hi(v) : 0u;
+                cnt[k] = 0;
+                dmax = max(dmax, d[k]);
+            }
+            // kAlg2Chunk entries of every vertex at a time: their ancestors,
+            // the ancestors' tree parents and the tested intervals are each
+            // loaded together
+            for (int c = 0; c < dmax; c += kAlg2Chunk) {
+                int a[kWalks][kAlg2Chunk], na[kWalks][kAlg2Chunk];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k)
+#pragma unroll
+                    for (int j = 0; j < kAlg2Chunk; ++j)
+                        a[k][j] = (c + j < d[k]) ? checked_vertex(__ldg(gd.path + s0[k] + c + j), n, u, 12, p) : -1;
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k)
+#pragma unroll
+                    for (int j = 0; j < kAlg2Chunk; ++j)
+                        na[k][j] = (a[k][j] >= 0 && a[k][j] != u) ? NP32[4ll * a[k][j]] : -1;
+                int tx[kWalks][kAlg2Chunk];
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+#pragma unroll
+                    for (int j = 0; j < kAlg2Chunk; ++j) {
+                        // edge (a_{c+j+1}, a_{c+j}): b = a_{c+j} (v itself first)
+                        const int aj = a[k][j];
+                        const int bj = (j == 0) ? prev[k] : a[k][j - 1];
+                        const int nbj = (j == 0) ? nprev[k] : na[k][j - 1];
+                        tx[k][j] = -1;  // no interval to test; a sign is folded into the vertex id below
+                        if (aj < 0) continue;
+                        if (nbj == aj) {  // downwards: the interval of b
+                            if (c + j == 0)
+                                cnt[k] += 1;  // v lies in its own subtree
+                            else
+                                tx[k][j] = bj;
+                        } else if (na[k][j] == bj && c + j > 0) {  // upwards: the interval of a
+                            tx[k][j] = -2 - aj;
                         }
                     }
                 }
-                int lo[kPairs], sz[kPairs], pv[kPairs];
-    #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    lo[k] = (sg[k] != 0) ? (int)(uint32_t)JA[tx[k]] : 0;
-                    sz[k] = (sg[k] != 0) ? (SM ? (int)(C[tx[k]] & 0xFFFFu) : (int)(P[tx[k]] & 0xFFFFFFFFull)) + 1 : 0;
-                    pv[k] = (sg[k] != 0) ? (int)(uint32_t)JA[v[k]] : 0;
-                }
-    #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    // lanes testing entries of the same vertex add up first, then
-                    // one of them updates R (consecutive entries share an owner)
-                    if (sg[k] != 0 && lo[k] <= pv[k] && pv[k] < lo[k] + sz[k]) {
-                        if (p.R_direct)
-                            atomicAdd(p.R_direct + gd.voff + v[k], (unsigned long long)(long long)sg[k]);
-                        else
-                            atomicAdd(Rp + v[k], sg[k]);
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k) {
+#pragma unroll
+                    for (int j = 0; j < kAlg2Chunk; ++j) {
+                        const int t = tx[k][j];
+                        if (t == -1) continue;
+                        const int vt = t >= 0 ? t : -2 - t;
+                        const unsigned long long w = *W.w(vt);
+                        const uint32_t lo = (uint32_t)(w >> 32), sz = (uint32_t)w + 1u;
+                        if (lo <= pv[k] && pv[k] - lo < sz) cnt[k] += (t >= 0) ? 1 : -1;
                     }
+#pragma unroll
+                    for (int j = 0; j < kAlg2Chunk; ++j)
+                        if (a[k][j] >= 0) {
+                            prev[k] = a[k][j];
+                            nprev[k] = na[k][j];
+                        }
                 }
             }
-        } else {
-            // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u. Per chunk of edges the
-            // ancestors, their successors and the tested intervals are loaded
-            // independently of each other.
-            for (int v = tid; v < n; v += BT) {
-                if (v == u) continue;
-                const int pv = (int)(uint32_t)JA[v];
-                const int s0 = __ldg(gd.pathptr + v);
-                const int d = __ldg(gd.pathptr + v + 1) - s0;
-                int prevb = v, prevnb = nxt[v];
-                int cnt = 0;
-                for (int c = 0; c < d; c += kPathChunk) {
-                    int a[kPathChunk], na[kPathChunk], tx[kPathChunk], sg[kPathChunk];
-    #pragma unroll
-                    for (int j = 0; j < kPathChunk; ++j) a[j] = (c + j < d) ? __ldg(gd.path + s0 + c + j) : -1;
-    #pragma unroll
-                    for (int j = 0; j < kPathChunk; ++j) na[j] = (a[j] >= 0) ? nxt[a[j]] : -2;
-    #pragma unroll
-                    for (int j = 0; j < kPathChunk; ++j) {
-                        const int b = (j == 0) ? prevb : a[j - 1];
-                        const int nb = (j == 0) ? prevnb : na[j - 1];
-                        tx[j] = -1;
-                        sg[j] = 0;
-                        if (a[j] >= 0) {
-                            if (nb == a[j]) {
-                                tx[j] = b;
-                                sg[j] = 1;
-                            } else if (na[j] == b) {
-                                tx[j] = a[j];
-                                sg[j] = -1;
-                            }
-                        }
-                    }
-                    int lo[kPathChunk], sz[kPathChunk];
-    #pragma unroll
-                    for (int j = 0; j < kPathChunk; ++j) {
-                        lo[j] = (sg[j] != 0) ? (int)(uint32_t)JA[tx[j]] : 0;
-                        sz[j] = (sg[j] != 0) ? (SM ? (int)(C[tx[j]] & 0xFFFFu) : (int)(P[tx[j]] & 0xFFFFFFFFull)) + 1 : 0;
-                    }
-    #pragma unroll
-                    for (int j = 0; j < kPathChunk; ++j)
-                        if (sg[j] != 0 && lo[j] <= pv && pv < lo[j] + sz[j]) cnt += sg[j];
-                    prevb = a[kPathChunk - 1];
-                    prevnb = na[kPathChunk - 1];
-                }
+#pragma unroll
+            for (int k = 0; k < kWalks; ++k) {
+                const int v = b0 + k * BT;
+                if (v >= n || v == u) continue;
                 if (p.R_direct) {
-                    if (cnt != 0) atomicAdd(p.R_direct + gd.voff + v, (unsigned long long)(long long)cnt);
+                    if (cnt[k] != 0)
+                        atomicAdd(p.R_direct + gd.voff + orig_of(gd, v), (unsigned long long)(long long)cnt[k]);
                 } else {
-                    Rp[v] += cnt;
+                    Rp[v] += cnt[k];
                 }
             }
         }
@@ -781,7 +920,6 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_kerne
         for (int k = 0; k < 8; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
     }
 }
-
 // ---------------------------------------------------------------------------
 // The same three phases for graphs of at most kTierMaxVertices vertices
 // (ids below 0xFFFF), with the hot per-tree state in shared memory (4 bytes
@@ -1450,12 +1588,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 }
 
 // out[v] += sum over partial rows of Rp[c][v] (exact, fixed order).
-__global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict__ Rp, long long *__restrict__ out)
+// Row v of Rp belongs to input vertex orig[v] (v itself when orig is NULL).
+__global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict__ Rp, long long *__restrict__ out,
+                                     const int32_t *__restrict__ orig)
 {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         long long s = 0;
         for (int c = 0; c < rows; ++c) s += Rp[(long long)c * n + v];
-        out[v] += s;
+        out[orig ? orig[v] : v] += s;
     }
 }
 
@@ -1467,10 +1607,22 @@ size_t smem_bytes_for(int max_n) { return (size_t)((max_n + 1) / 2) * 2 * sizeof
 
 int64_t stride_for(int max_n) { return ((int64_t)max_n + 2 + 31) / 32 * 32; }
 
+// Counter words the large-graph sampler keeps in shared memory at BT threads
+// per CTA: as many as the CTAs that fill one SM's 228 KB leave each after
+// 1 KB reserved per CTA, the kernel's own variables and the preorder chunk.
+constexpr int large_hot_cap(int bt) { return bt >= 1024 ? 26 * 1024 : bt == 512 ? 12 * 1024 : 4864; }
+static_assert(26 * 1024 <= kLargeHotMax, "the relabelling puts at least this many top vertices first");
+static_assert((26 * 1024 + kPreChunk) * 8 + 256 <= 227 * 1024, "hot words and chunk fit one CTA's shared memory");
+
+size_t large_smem_bytes(const SampleParams &p)
+{
+    return ((size_t)std::max(1, std::min(p.hot, p.max_n)) + kPreChunk) * 8;
+}
+
 // Graphs of at most kSmemMaxN vertices run the shared-memory kernel at any
 // shape; up to kTierMaxVertices the same kernel with its last words in the
-// workspace tail; larger graphs the global-memory kernel, built for 256
-// threads and more.
+// workspace tail; larger graphs the large-graph kernel, built for 256
+// threads and more, with p.hot counter words in shared memory.
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
@@ -1487,10 +1639,16 @@ cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
         if (e != cudaSuccess) return e;
         sample_aggregate_smem_kernel<BT, true><<<grid, BT, bytes, st>>>(p);
     } else {
-        if constexpr (BT >= 256)
-            sample_aggregate_kernel<BT, false><<<grid, BT, 0, st>>>(p);
-        else
+        if constexpr (BT >= 256) {
+            if (p.hot > large_hot_cap(BT)) return cudaErrorInvalidValue;
+            const size_t bytes = large_smem_bytes(p);
+            cudaError_t e = cudaFuncSetAttribute(sample_aggregate_large_kernel<BT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            if (e != cudaSuccess) return e;
+            sample_aggregate_large_kernel<BT><<<grid, BT, bytes, st>>>(p);
+        } else {
             return cudaErrorInvalidConfiguration;
+        }
     }
     return cudaGetLastError();
 }
@@ -1531,7 +1689,14 @@ int resident_ctas(int max_n)
             return 0;
     } else {
         if constexpr (BT >= 256) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_kernel<BT, false>, BT, 0) !=
+            SampleParams q{};
+            q.max_n = max_n;
+            q.hot = large_hot_cap(BT);
+            const size_t bytes = large_smem_bytes(q);
+            if (cudaFuncSetAttribute(sample_aggregate_large_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes) != cudaSuccess)
+                return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_large_kernel<BT>, BT, bytes) !=
                 cudaSuccess)
                 return 0;
         }
@@ -1558,10 +1723,9 @@ int default_bt(int max_n)
     if (max_n <= 8192) return 128;
     if (max_n <= 14336) return 256;
     if (max_n <= 28672) return 512;
-    if (max_n <= kTierMaxVertices) return 1024;
-    // above the shared-memory sampler: two trees per SM while the per-tree
-    // arrays are small, one whole-SM tree per SM for the very large graphs
-    return max_n <= 262144 ? 512 : 1024;
+    // above: one whole-SM tree per SM, which leaves the most shared memory
+    // for the hot counter words of the large-graph sampler
+    return 1024;
 }
 
 bool valid_bt(int bt) { return bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
@@ -1619,25 +1783,131 @@ int alloc_batch_sampler(Ctx *c, int block_threads, int ctas_per_sm)
     int64_t ws = 0;
     for (int k = 0; k < kNumClasses; ++k) {
         if (c->class_maxn[k] <= 0) continue;
-        const int rc = choose_cfg(c, c->class_maxn[k], block_threads, ctas_per_sm, &c->class_cfg[k]);
+        // a tuned class keeps its shape unless the caller fixed one
+        const bool tuned = c->class_tuned[k].bt > 0 && block_threads == 0 && ctas_per_sm == 0;
+        const int bt = tuned ? c->class_tuned[k].bt : block_threads;
+        const int cps = tuned ? c->class_tuned[k].ctas / std::max(1, c->num_sms) : ctas_per_sm;
+        const int rc = choose_cfg(c, c->class_maxn[k], bt, cps, &c->class_cfg[k]);
         if (rc) return rc;
         ws = std::max<int64_t>(ws, (int64_t)c->class_cfg[k].ctas * kWsArrays * stride_for(c->class_maxn[k]));
     }
     return reserve_workspace(c, ws, 0);
 }
 
-int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
-                int32_t *d_pops_out, int64_t *draws, int64_t *rounds, int *max_rounds, int *max_depth)
-{
-    if (t1 <= t0) return UST_OK;
-    if (t0 < 0 || t1 > (int64_t)0xFFFFFFFFll) return fail(c, UST_EINVAL, "tree ids must lie in [0, 2^32)");
-    const int mode = d_next_out ? 1 : 0;
-    const int grid = (int)std::min<int64_t>(c->cfg.ctas, t1 - t0);
-    if (mode == 0)
-        UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
-    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
+// ---------------------------------------------------------------------------
+// Launch-shape tuning (ust_opts.autotune). A sampler launch's shape, threads
+// per CTA and resident CTAs per SM, changes its speed and never its counts.
+// Each candidate shape that fits is timed on the same probe of the launch's
+// own work items (their counts go to scratch and are discarded); the fastest
+// is kept, and remembered per workload key for the life of the process.
+namespace {
 
-    // the graph's descriptor: uploaded when B_u (pivot, path space) changed
+std::mutex g_tune_mutex;
+std::map<TuneKey, LaunchCfg> g_tune_cache;
+
+std::vector<LaunchCfg> tune_candidates(int num_sms, int max_n)
+{
+    std::vector<LaunchCfg> out;
+    for (int bt : {64, 128, 256, 512, 1024}) {
+        if (max_n > kTierMaxVertices && bt < 512) continue;  // the large-graph sampler needs its hot words
+        const int res = resident_ctas_for(bt, max_n);
+        if (res < 1) continue;
+        out.push_back(LaunchCfg{bt, num_sms * res});
+        if (res >= 2) out.push_back(LaunchCfg{bt, num_sms * (res / 2)});
+    }
+    return out;
+}
+
+// One probe launch of `items` work items over d_graphs / d_items; counts go
+// to d_scratch (indexed like a batch's R). *ms: its device time.
+int probe_launch(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, const long long *d_items, int ngraphs,
+                 long long items, int max_n, long long max_rounds, int64_t *d_scratch, float *ms)
+{
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
+    SampleParams p{};
+    p.max_n = max_n;
+    p.key0 = 0x5EEDu;  // any key: the probe's counts are discarded
+    p.key1 = 0x7E57u;
+    p.graphs = d_graphs;
+    p.ngraphs = ngraphs;
+    p.item_start = d_items;
+    p.total_items = items;
+    p.tree_offset = 0;
+    p.ws = c->d_ws;
+    p.stride = stride_for(max_n);
+    p.Rp = c->d_Rp;
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(c->d_stats);
+    p.next_tree = st + 4;
+    p.stats = st;
+    p.status = reinterpret_cast<int *>(st + 5);
+    p.max_rounds = (int)std::min<long long>(max_rounds, 1ll << 30);
+    int lg = 0;
+    while ((1ll << lg) < (long long)max_n) ++lg;
+    p.max_steps = lg + 4;
+    p.mode = 0;
+    p.R_direct = reinterpret_cast<unsigned long long *>(d_scratch);
+    p.hot = large_hot_cap(cfg.bt);
+    const int grid = (int)std::min<long long>(cfg.ctas, items);
+    if ((int64_t)grid * kWsArrays * p.stride > c->ws_cap) return fail(c, UST_ECUDA, "tuning probe: workspace too small");
+    cudaEvent_t e0 = c->ev[2 * Ctx::kEvSample], e1 = c->ev[2 * Ctx::kEvSample + 1];
+    UST_CUDA_TRY(cudaEventRecord(e0, c->stream));
+    const cudaError_t e = launch_shape(cfg, grid, c->stream, p);
+    UST_CUDA_TRY(cudaEventRecord(e1, c->stream));
+    c->launches += 1;
+    if (e != cudaSuccess) return fail(c, UST_ECUDA, std::string("tuning probe launch: ") + cudaGetErrorString(e));
+    UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 32 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->h_stats[5] & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
+    if (c->h_stats[5])
+        return fail(c, UST_ECUDA, "sampler reported an inconsistent state (check " + std::to_string(c->h_stats[6]) + ")");
+    UST_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return UST_OK;
+}
+
+}  // namespace
+
+int tune_launch(Ctx *c, const TuneKey &key, const GraphDesc *d_graphs, const long long *d_items, int ngraphs,
+                long long items, int max_n, long long max_rounds, int64_t *d_scratch, LaunchCfg *out,
+                double *best_ms_per_item)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        const auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            if (best_ms_per_item) *best_ms_per_item = 0.0;
+            return UST_OK;
+        }
+    }
+    const std::vector<LaunchCfg> cands = tune_candidates(c->num_sms, max_n);
+    if (cands.empty()) return fail(c, UST_EINVAL, "no sampler launch shape fits this graph");
+    int64_t ws = 0;
+    for (const LaunchCfg &k : cands)
+        ws = std::max<int64_t>(ws, std::min<int64_t>(k.ctas, items) * kWsArrays * stride_for(max_n));
+    int rc = reserve_workspace(c, ws, 0);
+    if (rc) return rc;
+    double best = 0.0;
+    for (const LaunchCfg &k : cands) {
+        float ms = 0.f;
+        rc = probe_launch(c, k, d_graphs, d_items, ngraphs, items, max_n, max_rounds, d_scratch, &ms);
+        if (rc) return rc;
+        const double per = (double)ms / (double)items;
+        if (best == 0.0 || per < best) {
+            best = per;
+            *out = k;
+        }
+    }
+    c->ev_used[Ctx::kEvSample] = false;  // the probes' events are not a sampling phase
+    if (best_ms_per_item) *best_ms_per_item = best;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = *out;
+    return UST_OK;
+}
+
+// The single graph's descriptor: uploaded when B_u (pivot, path space) or
+// the rows changed.
+int upload_single_desc(Ctx *c)
+{
     GraphDesc gd{};
     gd.n = c->n;
     gd.u = c->pivot;
@@ -1653,10 +1923,23 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     gd.powner = c->d_path + 2 * c->path_cap;
     gd.fc = (int)c->farness;
     gd.aoff = 0;
+    gd.orig = nullptr;
+    gd.rp_in = nullptr;
+    // the large-graph sampler's relabelled view (not with the walk rows of
+    // the biconnected-component variant, which the context swaps in)
+    const bool relabelled = c->relabel && !c->blocks;
+    if (relabelled) {
+        gd.u = c->spivot;
+        gd.rp = c->d_srp;
+        gd.ci = c->d_sci;
+        gd.path = c->d_spath;
+        gd.orig = c->d_orig;
+        gd.rp_in = c->d_rp;
+    }
     const GraphDesc &o = c->single_desc;
     const bool same = o.n == gd.n && o.u == gd.u && o.graph == gd.graph && o.rp == gd.rp && o.ci == gd.ci &&
                       o.bpar == gd.bpar && o.path == gd.path && o.pathptr == gd.pathptr && o.pchild == gd.pchild &&
-                      o.powner == gd.powner && o.fc == gd.fc;
+                      o.powner == gd.powner && o.fc == gd.fc && o.orig == gd.orig && o.rp_in == gd.rp_in;
     if (!c->single_desc_valid || !same) {
         c->single_desc = gd;
         const long long starts[2] = {0, kOpenEnd};
@@ -1665,6 +1948,23 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         UST_CUDA_TRY(cudaMemcpyAsync(c->d_items, starts, sizeof(starts), cudaMemcpyHostToDevice, c->stream));
         c->single_desc_valid = true;
     }
+    return UST_OK;
+}
+
+int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,
+                int32_t *d_pops_out, int64_t *draws, int64_t *rounds, int *max_rounds, int *max_depth)
+{
+    if (t1 <= t0) return UST_OK;
+    if (t0 < 0 || t1 > (int64_t)0xFFFFFFFFll) return fail(c, UST_EINVAL, "tree ids must lie in [0, 2^32)");
+    const int mode = d_next_out ? 1 : 0;
+    const int grid = (int)std::min<int64_t>(c->cfg.ctas, t1 - t0);
+    if (mode == 0)
+        UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
+    UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
+
+    const int drc = upload_single_desc(c);
+    if (drc) return drc;
+    const bool relabelled = c->relabel && !c->blocks;
     SampleParams p{};
     p.max_n = c->n;
     p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
@@ -1695,6 +1995,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     p.mode = mode;
     p.next_out = d_next_out;
     p.pops_out = d_pops_out;
+    p.hot = large_hot_cap(c->cfg.bt);
 
     phase_begin(c, Ctx::kEvSample);
     const cudaError_t e = launch_shape(c->cfg, grid, c->stream, p);
@@ -1706,7 +2007,8 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         const int threads = 256;
         const int blocks = (int)std::min<int64_t>((c->n + threads - 1) / threads, (int64_t)c->num_sms * 8);
         reduce_counts_kernel<<<blocks, threads, 0, c->stream>>>(c->n, grid, c->d_Rp,
-                                                                 reinterpret_cast<long long *>(d_out));
+                                                                 reinterpret_cast<long long *>(d_out),
+                                                                 relabelled ? c->d_orig : nullptr);
         phase_end(c, Ctx::kEvReduce);
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
@@ -1716,7 +2018,8 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     const int status = (int)c->h_stats[5];
     if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
     if (status & kStatusJumpSteps) return fail(c, UST_ETIMEOUT, "pointer jumping did not converge");
-    if (status) return fail(c, UST_ECUDA, "sampler reported an inconsistent state");
+    if (status)
+        return fail(c, UST_ECUDA, "sampler reported an inconsistent state (check " + std::to_string(c->h_stats[6]) + ")");
     c->last_trees = t1 - t0;
     c->last_draws = c->h_stats[0];
     for (int k = 0; k < 12; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
@@ -1866,8 +2169,8 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
                                                                        const int32_t *__restrict__ ci, int32_t *dist,
                                                                        int32_t *bpar, int32_t *pathptr, int32_t *path,
                                                                        int32_t *pchild, int32_t *powner,
-                                                                       int path_cap, int *status, GraphDesc *desc,
-                                                                       long long *item_start)
+                                                                       int path_cap, int *status, int *ecc_out,
+                                                                       GraphDesc *desc, long long *item_start)
 {
     if (threadIdx.x == 0) {
         GraphDesc d;
@@ -1885,11 +2188,13 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
         d.powner = powner;
         d.fc = 0;  // set below, once f^c(u) is known
         d.aoff = 0;
+        d.orig = nullptr;
+        d.rp_in = nullptr;
         *desc = d;
         item_start[0] = 0;
         item_start[1] = kOpenEnd;
     }
-    prepare_graph(n, u, rp, ci, dist, bpar, pathptr, path, pchild, powner, path_cap, status, nullptr, &desc->fc);
+    prepare_graph(n, u, rp, ci, dist, bpar, pathptr, path, pchild, powner, path_cap, status, ecc_out, &desc->fc);
 }
 
 // Device address of g_noalloc_scratch, looked up once per device.
@@ -1929,23 +2234,24 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
     // the previous call's contents stay in the array: clear what must start at zero
     if (cudaMemsetAsync(stats, 0, 32 * sizeof(unsigned long long), st) != cudaSuccess) return UST_ECUDA;
     if (cudaMemsetAsync(Rp, 0, (size_t)kNoAllocCtas * n * sizeof(int32_t), st) != cudaSuccess) return UST_ECUDA;
-    if (cudaMemsetAsync(R_out, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess) return UST_ECUDA;
     int *status = reinterpret_cast<int *>(stats + 5);
+    int *ecc_dev = reinterpret_cast<int *>(stats + 6);
     GraphDesc *desc = reinterpret_cast<GraphDesc *>(base + kNaDesc);
     long long *item_start = reinterpret_cast<long long *>(desc + 1);
     noalloc_prepare_kernel<<<1, kPrepThreads, 0, st>>>(n, pivot, (uint32_t)graph_id, row_ptr, col_idx, dist, bpar,
                                                         pathptr, path, path + kNoAllocMaxPath,
-                                                        path + 2 * kNoAllocMaxPath, kNoAllocMaxPath, status, desc,
-                                                        item_start);
+                                                        path + 2 * kNoAllocMaxPath, kNoAllocMaxPath, status, ecc_dev,
+                                                        desc, item_start);
     if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
     unsigned long long h_stats[32];
     if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess) return UST_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return UST_ECUDA;
     if (h_stats[5] & 1) return UST_ENOTCONNECTED;
     if (h_stats[5] & 2) return UST_EINVAL;  // f^c(u) beyond the fixed scratch array
-    int ecc = 0;
+    // the checks passed: only now is R_out written
+    if (cudaMemsetAsync(R_out, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess) return UST_ECUDA;
     if (t1 > t0) {
-        ecc = n;  // upper bound on ecc(u), used only for the popping-round limit
+        const int ecc = std::max(1, (int)(uint32_t)h_stats[6]);  // ecc(u) from B_u: the popping-round limit
         SampleParams p{};
         p.max_n = n;
         p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
@@ -1970,7 +2276,8 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
         p.pops_out = nullptr;
         const int grid = (int)std::min<int64_t>(kNoAllocCtas, t1 - t0);
         if (launch_sampler<kNoAllocThreads>(grid, st, p) != cudaSuccess) return UST_ECUDA;
-        reduce_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, grid, Rp, reinterpret_cast<long long *>(R_out));
+        reduce_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, grid, Rp, reinterpret_cast<long long *>(R_out),
+                                                                nullptr);
         if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
         if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return UST_ECUDA;
@@ -2082,6 +2389,7 @@ int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, c
     p.total_items = total_items;
     p.R_direct = reinterpret_cast<unsigned long long *>(d_R);
     p.edge_counts = reinterpret_cast<unsigned long long *>(c->d_ecount_tmp);
+    p.hot = large_hot_cap(cfg.bt);
     const int grid = (int)std::min<long long>(cfg.ctas, total_items);
     phase_begin(c, Ctx::kEvSample);
     const cudaError_t e = launch_shape(cfg, grid, c->stream, p);
@@ -2093,7 +2401,8 @@ int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, c
     const int status = (int)c->h_stats[5];
     if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
     if (status & kStatusJumpSteps) return fail(c, UST_ETIMEOUT, "pointer jumping did not converge");
-    if (status) return fail(c, UST_ECUDA, "sampler reported an inconsistent state");
+    if (status)
+        return fail(c, UST_ECUDA, "sampler reported an inconsistent state (check " + std::to_string(c->h_stats[6]) + ")");
     c->last_trees = total_items;
     c->last_draws = c->h_stats[0];
     for (int k = 0; k < 12; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];

@@ -300,6 +300,8 @@ def workload(name: str):
     rmat17      R-MAT scale 17, edge factor 16, LCC, max-degree pivot, 1024 trees
                 (the smallest R-MAT above 65,535 vertices: a profiling case
                 of the large-graph sampler)
+    rmat19      R-MAT scale 19, edge factor 16, LCC, max-degree pivot, 1024 trees
+                (per-tree state far larger than L2, as for scale 22)
     hyperbolic20  threshold RHG n = 2^20, avg degree 20, gamma 3, eps 0.3
     rmat22      R-MAT scale 22, edge factor 16, LCC, max-degree pivot, eps 0.3
     """
@@ -310,6 +312,9 @@ def workload(name: str):
         return g, max_degree_vertex(g), 4096, None
     if name == "rmat17":
         g = rmat(17, 16, seed=1)
+        return g, max_degree_vertex(g), 1024, None
+    if name == "rmat19":
+        g = rmat(19, 16, seed=1)
         return g, max_degree_vertex(g), 1024, None
     if name == "rmat22":
         g = rmat(22, 16, seed=1)

@@ -40,8 +40,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_binding_structs_match_header_layout(lib):
     from paper_2006_13679_gb300 import _binding
-    # ust_opts: 3 doubles, 7 int32 (+4 padding), pointer -> 3*8 + 7*4 + 4 + 8 = 64 bytes
-    assert ctypes.sizeof(_binding.ust_opts) == 64
+    # ust_opts: 3 doubles, 9 int32 (+4 padding), pointer -> 3*8 + 9*4 + 4 + 8 = 72 bytes
+    assert ctypes.sizeof(_binding.ust_opts) == 72
     assert ctypes.sizeof(_binding.ust_csr) == 32  # 2 int32, 2 pointers, int32 + padding
     o = _binding.default_opts()
     assert o.kappa == 0.3 and o.cg_tol == 1e-9 and o.skip_validation == 0

@@ -128,3 +128,25 @@ def test_batch_edge_counts(pkg, orc):
         for i, g in enumerate(gs):
             assert np.array_equal(got[off:off + g.nnz], orc.edge_counts(g, piv[i], 0, 40, 6, graph=5 + i)), i
             off += g.nnz
+
+
+def test_tuned_and_fixed_launch_shapes_give_equal_counts(pkg, orc):
+    """The launch-shape tuner (ust_opts.autotune) changes only the speed of a
+    launch: a batch tuned at creation (the default for batches) and one on the
+    fixed shape table give identical counts, and a tuned single graph gives
+    the oracle's counts."""
+    gs, piv = small_batch()
+    graphs = [(g.row_ptr, g.col_idx) for g in gs]
+    with pkg.USTBatch(graphs, piv, autotune=1) as a, pkg.USTBatch(graphs, piv, autotune=-1) as b:
+        a.sample_aggregate(50, 3)
+        b.sample_aggregate(50, 3)
+        assert np.array_equal(a.counts(), b.counts())
+        shapes = {(a.graph_info(i)["sample_threads"], a.graph_info(i)["sample_ctas"]) for i in range(len(gs))}
+        assert all(bt in (64, 128, 256, 512, 1024) and ctas > 0 for bt, ctas in shapes)
+    g = synth.er(9000, 10.0, seed=7)
+    u = synth.max_degree_vertex(g)
+    with pkg.UST(g.row_ptr, g.col_idx, u, autotune=1) as h:
+        h.sample_aggregate(200, 5)
+        _, _, par = orc.bfs(g, u)
+        R_ref, _ = orc.sample_aggregate(g, u, par, 0, 200, 5, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)

@@ -7,8 +7,9 @@ compute one by one.
   tau from eps = 0.3
 
 Checked: B_u bit-exact, tau(0.3), single trees spread over [0, tau)
-bit-exact with their pop counts, the counts of a short tree range
-bit-exact, the column against FP64 CG within 1e-8, and the diagonal
+bit-exact with their pop counts, the counts of the last 2 x 152 tree ids
+below tau bit-exact (every CTA of the 152-SM launch samples at least two
+trees), the column against FP64 CG within 1e-8, and the diagonal
 combination within 1e-12 of the oracle's on the same counts and column.
 """
 import os
@@ -22,6 +23,7 @@ pytestmark = pytest.mark.gpu
 
 THREADS = max(1, min(16, os.cpu_count() or 1))
 SEED = 0x5EED
+RANGE_TREES = 2 * 152  # two trees for every CTA of a one-CTA-per-SM launch on 152 SMs
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +54,7 @@ def test_large_workload(pkg, orc, name):
             ref, ref_pops, _ = orc.wilson(g, u, t, SEED)
             assert np.array_equal(nxt[0], ref), (name, t)
             assert np.array_equal(pops[0], ref_pops), (name, t)
-        t0 = tau - 3
+        t0 = tau - RANGE_TREES
         R = h.tree_range_counts(t0, tau, SEED)
         R_ref, _ = orc.sample_aggregate(g, u, p_ref, t0, tau, SEED, threads=THREADS)
         assert np.array_equal(R, R_ref)

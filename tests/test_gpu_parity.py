@@ -132,7 +132,7 @@ def test_edge_graphs(pkg, orc, maker, u):
             assert np.array_equal(h.counts(), 301 * dist.astype(np.int64))
 
 
-@pytest.mark.parametrize("bt,cps", [(256, 1), (256, 8), (512, 2), (1024, 1)])
+@pytest.mark.parametrize("bt,cps", [(64, 0), (128, 0), (256, 1), (256, 8), (512, 2), (1024, 1)])
 def test_launch_configurations_agree(pkg, orc, bt, cps):
     g, u = GRAPHS["rmat12"]()
     with make(pkg, g, u, block_threads=bt, ctas_per_sm=cps) as h:
@@ -257,6 +257,21 @@ def test_counts_above_shared_memory_limit(pkg, orc, maker):
         for i in range(3):
             ref, ref_pops, _ = orc.wilson(g, u, 100 + i, 21)
             assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
+
+
+@pytest.mark.parametrize("bt,cps", [(512, 1), (512, 2), (1024, 1)])
+def test_large_sampler_shapes_agree(pkg, orc, bt, cps):
+    """The large-graph sampler at every shape the launch tuner may pick (its
+    shared-memory hot set shrinks with the threads per CTA): R and the draws
+    bit-exact."""
+    g = synth.rmat(17, 8, seed=2)
+    u = synth.max_degree_vertex(g)
+    with make(pkg, g, u, block_threads=bt, ctas_per_sm=cps) as h:
+        h.sample_aggregate(300, 13)
+        _, _, par = orc.bfs(g, u)
+        R_ref, steps = orc.sample_aggregate(g, u, par, 0, 300, 13, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert h.info()["draws"] == steps
 
 
 @pytest.mark.parametrize("maker,bt", [
