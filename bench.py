@@ -87,8 +87,10 @@ def phase_names(n: int):
             "aggregation", "tree_total"]
 
 
-# One-tree-per-launch comparator: trees timed (the rest extrapolated).
+# One-tree-per-launch comparator: trees timed (the rest extrapolated); fewer on
+# graphs above 65,535 vertices, where one tree on one CTA takes tens of milliseconds.
 COMPARATOR_TREES = 1024
+COMPARATOR_TREES_LARGE = 64
 
 
 def sampler_kernel(n: int) -> str:
@@ -350,7 +352,8 @@ def run_batch_gpu(args, rank: int, world: int, local_rank: int, dist) -> None:
             with torch.cuda.stream(stream):
                 dist.all_reduce(counts_d)
             b.set_counts(counts_d, world * T)
-        b.diag(0.0, diag_d)           # every graph's column solve + combination
+        if dist is None or rank == 0:  # every graph's column solve + combination, on one rank
+            b.diag(0.0, diag_d)
 
     for _ in range(args.warmup):
         step()
@@ -533,6 +536,10 @@ def main() -> None:
     ap.add_argument("--wilson-blocks", action="store_true",
                     help="single-graph workloads: walks inside each vertex's parent block "
                          "(the biconnected-component variant)")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="single-graph workloads: threads per sampling CTA (0 = the library's choice)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0,
+                    help="single-graph workloads: sampling CTAs per SM (0 = the library's choice)")
     ap.add_argument("--trees", type=int, default=0,
                     help="single-graph workloads: trees per step instead of the workload's own count")
     ap.add_argument("--per-class", action="store_true",
@@ -573,7 +580,8 @@ def main() -> None:
     stream = torch.cuda.Stream()
     rp_d = torch.from_numpy(g.row_ptr).cuda()
     ci_d = torch.from_numpy(g.col_idx).cuda()
-    h = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, wilson_blocks=args.wilson_blocks)
+    shape = dict(block_threads=args.block_threads, ctas_per_sm=args.ctas_per_sm)
+    h = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, wilson_blocks=args.wilson_blocks, **shape)
     # trees per step: the workload's fixed count, else tau(eps) of Algorithm 1 (ust_tau)
     T = args.trees if args.trees > 0 else (T0 if T0 is not None else h.tau(eps))
     gather = gather_peaks(pkg, stream)
@@ -585,10 +593,10 @@ def main() -> None:
         h.reset(u)                    # B_u, ecc, clear R
         if dist is None:
             h.sample_aggregate(T, seed)   # Wilson + intervals + Algorithm 2 + exact reduction
-        else:                         # this rank's tree ids, counts summed over ranks and installed
-            with torch.cuda.stream(stream):
-                parallel.sample_sharded(h, T, seed, out=counts_d)
-        h.diag(0.0, diag_d)           # column solve + combination
+            h.diag(0.0, diag_d)           # column solve + combination
+        else:                         # rank 0 solves the column; every rank samples its tree ids;
+            with torch.cuda.stream(stream):  # counts summed and installed; rank 0 combines
+                parallel.diag_sharded(h, T, seed, out=diag_d, counts_out=counts_d)
 
     for _ in range(args.warmup):
         step()
@@ -647,7 +655,7 @@ def main() -> None:
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with pkg.UST(g.row_ptr, g.col_idx, u, wilson_blocks=args.wilson_blocks) as he:
+        with pkg.UST(g.row_ptr, g.col_idx, u, wilson_blocks=args.wilson_blocks, **shape) as he:
             he.sample_aggregate(T, seed)
             d_host = he.diag()
         t1 = time.perf_counter()
@@ -666,8 +674,8 @@ def main() -> None:
     comparator = None
     if not args.no_comparator:
         hc = pkg.UST(rp_d, ci_d, u, stream=stream, skip_validation=True, solve_fp64=True,
-                     wilson_blocks=args.wilson_blocks)
-        tc = min(T, COMPARATOR_TREES)
+                     wilson_blocks=args.wilson_blocks, **shape)
+        tc = min(T, COMPARATOR_TREES if g.n <= 0xFFFF else COMPARATOR_TREES_LARGE)
         torch.cuda.synchronize()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)

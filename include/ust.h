@@ -109,7 +109,9 @@ typedef struct {
                                Single-graph contexts only (ust_init_batch: UST_EINVAL)
                                [0 = plain Wilson rooted at u] */
     int32_t autotune;       /* launch shapes of the sampler: 1 = tuned, -1 = fixed table, 0 = default
-                               [tuned for ust_init_batch, fixed for ust_init]. Tuning times every
+                               [tuned for ust_init_batch and for single graphs of at most 65,535
+                               vertices, fixed above (the large-graph sampler keeps 1,024 threads,
+                               the most shared memory for its hot words)]. Tuning times every
                                candidate shape (threads per CTA x CTAs per SM that fit) on a probe of
                                the launch's own work at context creation and keeps the fastest; the
                                choice is remembered for the process per workload key (kernel, size

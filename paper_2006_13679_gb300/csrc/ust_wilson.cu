@@ -2,8 +2,12 @@
 // spanning tree T rooted at u (Wilson's algorithm, Appendix A.2) and adds
 // its Algorithm 2 counts to R.
 //
-// One CTA owns one tree at a time and takes tree ids from a global counter
-// (persistent kernel). Per tree:
+// One CTA owns one tree at a time and takes work items (graph, tree) from a
+// global counter (persistent kernel). Two kernels share the method:
+// sample_aggregate_smem_kernel (graphs up to 65,535 vertices, per-tree words
+// in shared memory) and sample_aggregate_large_kernel (larger graphs, per-tree
+// records in the CTA's workspace, the highest-degree vertices' counters in
+// shared memory). Per tree:
 //
 //  1. Cycle popping (Wilson's cycle-popping theorem, used in Appendix A.2).
 //     Every vertex v != u has a stack of random neighbours, entry k being the
@@ -16,22 +20,25 @@
 //       its last in-edge, so it costs O(n) atomics and no barriers.
 //     - Later rounds: every new cycle passes through a vertex redrawn in the
 //       previous round. Each redrawn vertex x walks the stack tops until the
-//       next redrawn vertex S(x) or a vertex known to reach u. Cycles of the
-//       small graph x -> S(x) are found by min-label pointer jumping; their
-//       segments are the vertex cycles, which are popped (every vertex on
-//       them advances to its next stack entry). Segments that reach u are
-//       marked, so later walks stop there.
+//       next redrawn vertex S(x) or a vertex known to reach u; a walk that
+//       meets a vertex another walk of the round passed takes that walk's
+//       result. Each node of the small graph x -> S(x) is classified by
+//       Brent's cycle detection (reaches u, on a cycle, or runs into one); the
+//       cycle segments are popped (every vertex on them advances to its next
+//       stack entry), and the parts that reach u are marked final.
 //  2. DFS intervals of T (Algorithm 2's discovery/finish times), without
-//     level barriers: subtree sizes by a packed 64-bit "pending children |
-//     size" counter where the last arriving child carries the sum upwards;
-//     child offsets from an atomic cursor of the parent; preorder numbers by
-//     ancestor walks that stop at the first numbered ancestor and write the
-//     path back. Any child order gives valid nested intervals and the
-//     subtree test does not depend on it.
-//  3. Algorithm 2 with the inclusive subtree test: thread v walks P(v) up
-//     B_u and adds +1 / -1 for every BFS edge that T uses downwards /
-//     upwards above v. Counts go to the CTA's partial row Rp; a second kernel
-//     sums the partial rows into the int64 R exactly.
+//     level barriers: subtree sizes by a packed "pending children | summed
+//     sizes" word where the last arriving child carries the sum upwards; the
+//     same atomic gives each child its offset inside its parent's interval
+//     (any child order gives valid nested intervals). Preorder numbers are
+//     the root-path sums of the offsets: pointer jumping in shared memory
+//     (smem kernel), or top-down over the log of the arrivals read backwards,
+//     chunk by chunk (large kernel).
+//  3. Algorithm 2 with the inclusive subtree test over the flattened BFS paths
+//     P(v): one independent test per path entry (shallow paths) or a walk per
+//     vertex (deep paths, and every path in the large kernel). Counts go to
+//     the CTA's partial row, summed into the int64 R exactly by a second
+//     kernel in a fixed order (batches: int64 atomics).
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -177,14 +184,16 @@ constexpr int kThreadsPerSm = 1024;
 // Graphs above kTierMaxVertices vertices: the per-tree state lives in the
 // CTA's workspace, with the hottest counter words in shared memory.
 //
-// Per vertex v of the sampler's graph:
-//   NP(v)  high 32 bits: stack depth of the current top, then (after the
-//          sizes pass) v's offset inside its parent's interval; low 32 bits:
-//          the stack top, the tree parent at the end (-1 at u)
+// Per vertex v of the sampler's graph, two arrays of 64-bit words:
+//   NP(v)  high 32 bits: stack depth of the current top; low 32 bits: the
+//          stack top, the tree parent at the end (-1 at u)
 //   CW(v)  by phase: (children | in-edges removed by peeling),
 //          (children | round mark), (pending children | summed sizes),
 //          (preorder number | summed sizes)
-// CW words of the vertices below p.hot sit in shared memory. A single graph
+// Kept as two plain arrays rather than one 16-byte record per vertex, the
+// next tier of hubs stays compact enough for L2 (measured: 3.5% faster on
+// R-MAT scale 22). CW words of the vertices below p.hot sit in shared
+// memory. A single graph
 // is relabelled for the sampler so that these are the vertices of largest
 // degree: a uniformly drawn neighbour, and so most random successor,
 // counter and ancestor accesses, lands on them (on R-MAT scale 22 the
@@ -199,27 +208,30 @@ constexpr int kThreadsPerSm = 1024;
 //  3. the vertices left with in-edges lie on cycles: the first round list;
 //  4. popping rounds as in the shared-memory sampler, marks in the low words,
 //     children counts kept up to date in the high words;
-//  5. subtree sizes and offsets by last arrivers; every arrival is logged,
-//     so the log lists each vertex before its parent;
-//  6. preorder numbers top-down over the log in reverse: pre(x) = pre(parent)
-//     + offset(x); a vertex whose parent is not numbered yet is retried in a
-//     later pass (each pass numbers at least the shallowest one left);
+//  5. subtree sizes and offsets by last arrivers; every arrival (vertex,
+//     parent, offset) is logged, so the log lists each vertex before its
+//     parent;
+//  6. preorder numbers top-down over the log read backwards, chunk by chunk:
+//     pre(x) = pre(parent) + offset(x), links inside a chunk resolved by
+//     pointer jumping, the rare vertex whose parent comes later numbered in
+//     passes afterwards;
 //  7. Algorithm 2 per vertex over its flattened BFS path; the first edge
 //     (bfs_parent(v), v) needs no interval (v lies in its own subtree, and
 //     never below its own tree child).
 struct LargeWords {
     unsigned long long *s;  // shared: the words of vertices below hot
-    unsigned long long *g;  // global: CW of vertex v at g[2 v] (slots below hot unused)
+    unsigned long long *g;  // global: CW of vertex v at g[v] (slots below hot unused)
     int hot;
-    __device__ __forceinline__ unsigned long long *w(int v) const { return v < hot ? s + v : g + 2 * (long long)v; }
+    __device__ __forceinline__ unsigned long long *w(int v) const { return v < hot ? s + v : g + v; }
     __device__ __forceinline__ uint32_t *lo(int v) const { return reinterpret_cast<uint32_t *>(w(v)); }
     __device__ __forceinline__ uint32_t *hi(int v) const { return reinterpret_cast<uint32_t *>(w(v)) + 1; }
 };
 
-// Preorder phase: vertices per chunk (a packed shared word each), the tag
-// and link values of the high words, and the rounds a warp waits for the
-// parents of deferred vertices before leaving them to the next pass.
-constexpr int kPreChunk = 2048;
+// Preorder phase: vertices per chunk and thread (a packed word each in the
+// CTA's workspace), the tag and link values of the high words, and the
+// rounds a warp waits for the parents of deferred vertices before leaving
+// them to the next pass.
+constexpr int kPreChunkPerThread = 8;
 // Algorithm 2 entries per vertex loaded together in the large-graph sampler.
 constexpr int kAlg2Chunk = 2;
 constexpr uint32_t kPreTag = 0x80000000u;      // high word of a vertex of the current chunk
@@ -267,6 +279,24 @@ __device__ __forceinline__ int checked_vertex(int v, int n, int u, int site, con
     return u;
 }
 
+// Appends (x, parent, offset) at one position of three arrays, for the lanes
+// with flag set (at most cap entries). All 32 lanes must call it.
+__device__ __forceinline__ void warp_log_arrival(bool flag, int x, int par, int off, int32_t *qx, int32_t *qp,
+                                                 int32_t *qo, int *cnt, int cap)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int i = base + __popc(m & ((1u << lane) - 1u));
+    if (flag && i < cap) {
+        qx[i] = x;
+        qp[i] = par;
+        qo[i] = off;
+    }
+}
+
 // The same for 64-bit values.
 __device__ __forceinline__ void warp_append_pair(bool flag, unsigned long long val, unsigned long long *q, int *cnt,
                                                  int cap)
@@ -287,18 +317,17 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
     const int tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
-    // one 16-byte record per vertex (arrays 0 to 3): NP(v) at NP[2 v], CW(v)
-    // at NP[2 v + 1], so that an atomic on a vertex's CW word and the read of
-    // its NP word touch the same 32-byte sector
+    // NP(v) at NP[v] (arrays 0, 1), CW(v) at CWg[v] (arrays 2, 3)
     unsigned long long *NP = reinterpret_cast<unsigned long long *>(base);
-    int32_t *NP32 = base;  // NP32[4 v]: stack top / tree parent; NP32[4 v + 1]: depth / offset
-    unsigned long long *CWg = NP + 1;
+    int32_t *NP32 = base;  // NP32[2 v]: stack top / tree parent; NP32[2 v + 1]: depth / offset
+    unsigned long long *CWg = NP + S_;
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // round lists, then preorder retries
     int32_t *pos = base + 6 * S_;    // index of a redrawn vertex in the round's list
     int32_t *Sx = base + 7 * S_;     // S(x) as an index into the round's list, -1 = reaches u
     int32_t *owner = base + 8 * S_;  // the walk of this round that passed a vertex
     int32_t *wlen = base + 9 * S_;   // vertices a walk passed before it stopped
-    int32_t *ord = base + 10 * S_;   // arrivals of the sizes pass, in order
+    // the arrivals of the sizes pass, in order: vertex, tree parent, offset
+    int32_t *ord = base + 10 * S_, *ordp = base + 11 * S_, *ordo = base + 12 * S_;
     int32_t *Rp = p.Rp + (long long)blockIdx.x * p.max_n;
     constexpr unsigned long long kChild = 1ull << 32;
 
@@ -339,7 +368,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
 
         // ---- 1. first draws and in-degrees ---------------------------------
         for (int w = tid; w < W.hot; w += BT) s_hot[w] = 0ull;
-        for (int v = W.hot + tid; v < n; v += BT) CWg[2ll * v] = 0ull;
+        for (int v = W.hot + tid; v < n; v += BT) CWg[v] = 0ull;
         __syncthreads();
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
             int o[kWalks], rb[kWalks], deg[kWalks];
@@ -361,7 +390,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 if (v < n) {
-                    NP[2ll * v] = (unsigned long long)(uint32_t)y[k];
+                    NP[v] = (unsigned long long)(uint32_t)y[k];
                     if (y[k] >= 0 && y[k] != u) atomicAdd(W.w(checked_vertex(y[k], n, u, 1, p)), kChild);  // u's counters are never needed
                 }
             }
@@ -381,7 +410,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             if (tid == 0) s_qh = 0;
             for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
                 const bool leaf = v < n && v != u && (*W.w(v) >> 32) == 0ull;
-                const int y0 = leaf ? checked_vertex(NP32[4ll * v], n, u, 2, p) : u;
+                const int y0 = leaf ? checked_vertex(NP32[2ll * v], n, u, 2, p) : u;
                 warp_append_capped(leaf && y0 != u, y0, Q, &s_qn, n);
             }
             __syncthreads();
@@ -405,7 +434,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     ny[k] = u;
                     if (y[k] != u) {
                         old[k] = atomicAdd(W.w(y[k]), 1ull);
-                        ny[k] = checked_vertex(NP32[4ll * y[k]], n, u, 3, p);
+                        ny[k] = checked_vertex(NP32[2ll * y[k]], n, u, 3, p);
                     }
                 }
                 bool any = false;
@@ -464,11 +493,11 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             for (int i = tid; i < nX; i += BT) {
                 const int x = checked_vertex(X[i], n, u, 4, p);
                 if (x == u) continue;
-                const unsigned long long wx = NP[2ll * x];
+                const unsigned long long wx = NP[x];
                 const uint32_t k = (uint32_t)(wx >> 32) + 1u;
                 const int old = checked_vertex((int)(uint32_t)wx, n, u, 5, p);
                 const int y = checked_vertex(stack_entry_of(gd, p.key0, p.key1, x, orig_of(gd, x), k, tree), n, u, 5, p);
-                NP[2ll * x] = ((unsigned long long)k << 32) | (uint32_t)y;
+                NP[x] = ((unsigned long long)k << 32) | (uint32_t)y;
                 *W.lo(x) = (uint32_t)rounds;
                 pos[x] = i;
                 if (old != u) atomicAdd(W.hi(old), 0xFFFFFFFFu);  // one child less
@@ -487,11 +516,11 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             //     the mark, block fence), resolved after the barrier
             const int vis = -2 - rounds;
             for (int i = tid; i < nX; i += BT) {
-                int y = checked_vertex(NP32[4ll * checked_vertex(X[i], n, u, 6, p)], n, u, 6, p);
+                int y = checked_vertex(NP32[2ll * checked_vertex(X[i], n, u, 6, p)], n, u, 6, p);
                 int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = (int)*W.lo(y);
-                    const int ny = NP32[4ll * y];  // checked below, before it is used
+                    const int ny = NP32[2ll * y];  // checked below, before it is used
                     if (m == kFinal) {
                         res = -1;
                         break;
@@ -545,13 +574,13 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     const int len = wlen[i];
                     *W.lo(y) = (uint32_t)kFinal;
                     for (int k = 0; k < len; ++k) {
-                        y = checked_vertex(NP32[4ll * y], n, u, 8, p);
+                        y = checked_vertex(NP32[2ll * y], n, u, 8, p);
                         *W.lo(y) = (uint32_t)kFinal;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
                         Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
-                        y = checked_vertex(max(NP32[4ll * y], 0), n, u, 8, p);  // -1 at u: an inconsistent walk stays in the arrays
+                        y = checked_vertex(max(NP32[2ll * y], 0), n, u, 8, p);  // -1 at u: an inconsistent walk stays in the arrays
                         if ((int)*W.lo(y) == rounds) break;
                     }
                     if ((int)*W.lo(y) != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
@@ -581,7 +610,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 if (v == u) continue;
                 const int o = orig_of(gd, v);
                 const int b = __ldg(gd.rp + v), e = __ldg(gd.rp + v + 1);
-                const uint32_t k = (uint32_t)(NP[2ll * v] >> 32);
+                const uint32_t k = (uint32_t)(NP[v] >> 32);
                 const unsigned long long x = philox_x64((uint32_t)o, k, tree, gd.graph, p.key0, p.key1);
                 const long long row = gd.rp_in ? (long long)__ldg(gd.rp_in + o) : (long long)b;  // input arc index
                 atomicAdd(p.edge_counts + gd.aoff + row + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
@@ -590,7 +619,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         if (p.mode == 1) {  // export the tree in input ids
             const long long ob = s_tree * (long long)n;
             for (int v = tid; v < n; v += BT) {
-                const unsigned long long w = NP[2ll * v];
+                const unsigned long long w = NP[v];
                 const int o = orig_of(gd, v);
                 const int tp = (int)(uint32_t)w;
                 p.next_out[ob + o] = (tp < 0) ? -1 : orig_of(gd, tp);
@@ -622,7 +651,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(XA);
             for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
                 const bool leaf = v < n && v != u && *W.w(v) == 0ull;
-                const int pv = leaf ? checked_vertex(NP32[4ll * v], n, u, 9, p) : u;
+                const int pv = leaf ? checked_vertex(NP32[2ll * v], n, u, 9, p) : u;
                 warp_append_pair(leaf, ((unsigned long long)(uint32_t)v << 32) | (uint32_t)pv, Q2, &s_cnt, n);
             }
             __syncthreads();
@@ -642,8 +671,6 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             }
             bool done = false;
             for (int guard = 0; guard <= 2 * n + 2; ++guard) {
-#pragma unroll
-                for (int k = 0; k < kWalks; ++k) warp_append_capped(par[k] >= 0, x[k], ord, &s_qn, n);
                 unsigned long long old[kWalks];
                 int gp[kWalks];
 #pragma unroll
@@ -652,14 +679,18 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     gp[k] = -1;
                     if (par[k] >= 0) {
                         old[k] = atomicAdd(W.w(par[k]), (unsigned long long)carry[k] - kChild);
-                        if (par[k] != u) gp[k] = checked_vertex(NP32[4ll * par[k]], n, u, 10, p);
+                        if (par[k] != u) gp[k] = checked_vertex(NP32[2ll * par[k]], n, u, 10, p);
                     }
                 }
+                // log every arrival: x, its parent and its offset inside the
+                // parent's interval (all lanes call)
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k)
+                    warp_log_arrival(par[k] >= 0, x[k], par[k], 1 + (int)(uint32_t)old[k], ord, ordp, ordo, &s_qn, n);
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     if (par[k] >= 0) {
-                        NP32[4ll * x[k] + 1] = 1 + (int)(uint32_t)old[k];  // x's offset inside its parent's interval
                         if (par[k] != u && (old[k] >> 32) == 1ull) {    // the last child: carry the size upwards
                             carry[k] = (uint32_t)old[k] + carry[k] + 1u;
                             x[k] = par[k];
@@ -692,43 +723,56 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         // pre(u) = 0 and pre(x) = pre(parent) + offset(x) >= 1, written into
         // the high word (0 after the sizes pass: no child pending). The log
         // read backwards lists parents before their children; it is taken in
-        // chunks of kPreChunk vertices. A chunk's vertices are first tagged
+        // chunks of kPreChunkPerThread x BT vertices. A chunk's vertices are first tagged
         // (high word = kPreTag | position in the chunk); then each one finds
         // its parent numbered (an earlier chunk, or u), tagged (this chunk:
         // a link), or neither (a later chunk, which the log order makes rare:
         // deferred). Links are resolved by pointer jumping on packed
-        // (link, sum) words in shared memory, and the numbers written back.
+        // (link, sum) words in the CTA's workspace, and the numbers written back.
         // Deferred vertices are numbered afterwards in passes in which each
         // warp waits a bounded number of rounds for the parents; what is
         // still pending goes to the next pass.
         {
-            unsigned long long *s_chunk = s_hot + min(p.hot, p.max_n);  // kPreChunk packed words
+            // the chunk's packed words in the XB array (free until the
+            // deferred passes), L2-resident
+            volatile unsigned long long *chunk = reinterpret_cast<volatile unsigned long long *>(XB);
             const int total = n - 1;
+            const int K = min(kPreChunkPerThread * BT, (int)(S_ / 2));
             if (tid == 0) s_cnt = 0;  // deferred vertices, listed in XA
             __syncthreads();
-            for (int c0 = 0; c0 < total; c0 += kPreChunk) {
-                const int len = min(kPreChunk, total - c0);
+            for (int c0 = 0; c0 < total; c0 += K) {
+                const int len = min(K, total - c0);
                 for (int i = tid; i < len; i += BT) {
                     const int x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
                     *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = kPreTag | (uint32_t)i;
                 }
                 __syncthreads();
-                for (int i = tid; i < len; i += BT) {
-                    const int x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
-                    const unsigned long long w = NP[2ll * x];
-                    const int par = checked_vertex((int)(uint32_t)w, n, u, 13, p);
-                    const uint32_t off = (uint32_t)(w >> 32);
-                    uint32_t link = kPreRoot, sum = off;
-                    if (par != u) {
-                        const uint32_t h = *reinterpret_cast<volatile uint32_t *>(W.hi(par));
-                        if (h & kPreTag)
-                            link = h & ~kPreTag;  // the parent is in this chunk
-                        else if (h != 0u)
-                            sum = h + off;  // numbered in an earlier chunk
-                        else
-                            link = kPreDeferred;
+                for (int i0 = tid; i0 < len; i0 += BT * kWalks) {
+                    int par[kWalks];
+                    uint32_t off[kWalks], h[kWalks];
+#pragma unroll
+                    for (int k = 0; k < kWalks; ++k) {
+                        const int i = i0 + k * BT, j = total - 1 - (c0 + i);
+                        par[k] = (i < len) ? checked_vertex(ordp[j], n, u, 13, p) : u;
+                        off[k] = (i < len) ? (uint32_t)ordo[j] : 0u;
                     }
-                    s_chunk[i] = ((unsigned long long)link << 32) | sum;
+#pragma unroll
+                    for (int k = 0; k < kWalks; ++k)
+                        h[k] = (par[k] != u) ? *reinterpret_cast<volatile uint32_t *>(W.hi(par[k])) : 0u;
+#pragma unroll
+                    for (int k = 0; k < kWalks; ++k) {
+                        if (i0 + k * BT >= len) continue;
+                        uint32_t link = kPreRoot, sum = off[k];
+                        if (par[k] != u) {
+                            if (h[k] & kPreTag)
+                                link = h[k] & ~kPreTag;  // the parent is in this chunk
+                            else if (h[k] != 0u)
+                                sum = h[k] + off[k];  // numbered in an earlier chunk
+                            else
+                                link = kPreDeferred;
+                        }
+                        chunk[i0 + k * BT] = ((unsigned long long)link << 32) | sum;
+                    }
                 }
                 __syncthreads();
                 // pointer jumping: a word read while its owner rewrites it is
@@ -737,14 +781,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     bool any = false;
                     if (step <= 32) {
                         for (int i = tid; i < len; i += BT) {
-                            const unsigned long long a = s_chunk[i];
+                            const unsigned long long a = chunk[i];
                             const uint32_t l = (uint32_t)(a >> 32);
                             if (l >= kPreRoot) continue;  // resolved or deferred
-                            const unsigned long long b = s_chunk[l];
+                            const unsigned long long b = chunk[l];
                             const uint32_t l2 = (uint32_t)(b >> 32);
-                            s_chunk[i] = l2 == kPreDeferred ? ((unsigned long long)kPreDeferred << 32)
-                                                            : ((unsigned long long)l2 << 32) |
-                                                                  (uint32_t)((uint32_t)a + (uint32_t)b);
+                            chunk[i] = l2 == kPreDeferred ? ((unsigned long long)kPreDeferred << 32)
+                                                          : ((unsigned long long)l2 << 32) |
+                                                                (uint32_t)((uint32_t)a + (uint32_t)b);
                             any = true;
                         }
                     }
@@ -756,14 +800,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 }
                 for (int i = tid; i - (tid & 31) < len; i += BT) {  // uniform per warp
                     bool deferred = false;
-                    int x = -1;
+                    const int j = total - 1 - (c0 + i);
                     if (i < len) {
-                        x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
-                        const unsigned long long a = s_chunk[i];
+                        const int x = checked_vertex(ord[j], n, u, 11, p);
+                        const unsigned long long a = chunk[i];
                         deferred = (uint32_t)(a >> 32) != kPreRoot;
                         *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = deferred ? 0u : (uint32_t)a;
                     }
-                    warp_append_capped(deferred, x, XA, &s_cnt, n);
+                    warp_append_capped(deferred, j, XA, &s_cnt, n);  // the log position
                 }
                 __syncthreads();
             }
@@ -778,11 +822,13 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 if (tid == 0) s_cnt = 0;
                 __syncthreads();
                 for (int b0 = tid; b0 - (tid & 31) < cnt; b0 += BT) {  // uniform per warp
-                    const int x = (b0 < cnt) ? checked_vertex(list[b0], n, u, 11, p) : -1;
-                    const unsigned long long w = (x >= 0) ? NP[2ll * x] : 0ull;
-                    const int par = (x >= 0) ? checked_vertex((int)(uint32_t)w, n, u, 13, p) : u;
+                    const int j = (b0 < cnt) ? list[b0] : -1;
+                    const bool valid = (unsigned)j < (unsigned)total;
+                    const int x = valid ? checked_vertex(ord[j], n, u, 11, p) : -1;
+                    const int par = valid ? checked_vertex(ordp[j], n, u, 13, p) : u;
+                    const uint32_t off = valid ? (uint32_t)ordo[j] : 0u;
                     uint32_t pp = 0u;
-                    bool ok = x < 0 || par == u, written = x < 0;
+                    bool ok = !valid || par == u, written = !valid;
                     // the warp waits together, so a parent numbered by another
                     // lane is seen one round later
                     for (int spin = 0;; ++spin) {
@@ -791,12 +837,12 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                             ok = pp != 0u;
                         }
                         if (ok && !written) {
-                            *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = pp + (uint32_t)(w >> 32);
+                            *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = pp + off;
                             written = true;
                         }
                         if (__all_sync(0xffffffffu, written) || spin >= kPreorderSpin) break;
                     }
-                    warp_append_capped(!written, x, retry, &s_cnt, n);
+                    warp_append_capped(!written, j, retry, &s_cnt, n);
                 }
                 __syncthreads();
                 cnt = min(s_cnt, n);
@@ -830,7 +876,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 s0[k] = ok ? __ldg(gd.pathptr + o) : 0;
                 d[k] = ok ? __ldg(gd.pathptr + o + 1) - s0[k] : 0;
                 prev[k] = v;
-                nprev[k] = ok ? NP32[4ll * v] : -2;
+                nprev[k] = ok ? NP32[2ll * v] : -2;
                 pv[k] = ok ? *W.hi(v) : 0u;
                 cnt[k] = 0;
                 dmax = max(dmax, d[k]);
@@ -849,7 +895,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 for (int k = 0; k < kWalks; ++k)
 #pragma unroll
                     for (int j = 0; j < kAlg2Chunk; ++j)
-                        na[k][j] = (a[k][j] >= 0 && a[k][j] != u) ? NP32[4ll * a[k][j]] : -1;
+                        na[k][j] = (a[k][j] >= 0 && a[k][j] != u) ? NP32[2ll * a[k][j]] : -1;
                 int tx[kWalks][kAlg2Chunk];
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
@@ -1609,15 +1655,11 @@ int64_t stride_for(int max_n) { return ((int64_t)max_n + 2 + 31) / 32 * 32; }
 
 // Counter words the large-graph sampler keeps in shared memory at BT threads
 // per CTA: as many as the CTAs that fill one SM's 228 KB leave each after
-// 1 KB reserved per CTA, the kernel's own variables and the preorder chunk.
-constexpr int large_hot_cap(int bt) { return bt >= 1024 ? 26 * 1024 : bt == 512 ? 12 * 1024 : 4864; }
-static_assert(26 * 1024 <= kLargeHotMax, "the relabelling puts at least this many top vertices first");
-static_assert((26 * 1024 + kPreChunk) * 8 + 256 <= 227 * 1024, "hot words and chunk fit one CTA's shared memory");
+// 1 KB reserved per CTA and the kernel's own variables.
+constexpr int large_hot_cap(int bt) { return bt >= 1024 ? kLargeHotMax : bt == 512 ? 14336 : 7040; }
+static_assert(kLargeHotMax * 8 + 1024 + 256 <= 227 * 1024, "hot words fit one CTA's shared memory");
 
-size_t large_smem_bytes(const SampleParams &p)
-{
-    return ((size_t)std::max(1, std::min(p.hot, p.max_n)) + kPreChunk) * 8;
-}
+size_t large_smem_bytes(const SampleParams &p) { return (size_t)std::max(1, std::min(p.hot, p.max_n)) * 8; }
 
 // Graphs of at most kSmemMaxN vertices run the shared-memory kernel at any
 // shape; up to kTierMaxVertices the same kernel with its last words in the

@@ -7,6 +7,11 @@ integer rows are summed. The sum equals the counts of one GPU sampling all the
 trees, bit for bit. This is the paper's distributed scheme (Appendix D: trees
 spread over processes, R reduced at the end), with the graph replicated on
 every GPU. The sum is the only exchange of the path.
+
+The column L^+[:, u] depends on the graph and pivot only, so one rank (the
+solver rank) solves it, before the exchange, while the other ranks are still
+sampling; no other rank solves. The solver rank then combines the summed
+counts with its column into the diagonal.
 """
 from __future__ import annotations
 
@@ -37,3 +42,24 @@ def sample_sharded(ctx, trees_per_rank: int, seed: int, group=None, out=None):
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     ctx.set_counts(t if t.is_cuda else t.numpy(), world * trees_per_rank)
     return t
+
+
+def diag_sharded(ctx, trees_per_rank: int, seed: int, out=None, solver_rank: int = 0, group=None,
+                 counts_out=None):
+    """diag(L^+) from world * trees_per_rank trees spread over the ranks.
+
+    The solver rank solves the column first (``column()``: L^+[:, u] does not
+    depend on the trees), then every rank samples its tree range and the
+    counts are summed and installed (``sample_sharded``); the solver rank
+    alone forms the diagonal (``diag``) into `out` and returns it, the other
+    ranks return None. counts_out: optional int64 buffer for the counts.
+    """
+    import torch.distributed as dist
+
+    rank = dist.get_rank(group)
+    if rank == solver_rank:
+        ctx.column()
+    sample_sharded(ctx, trees_per_rank, seed, group=group, out=counts_out)
+    if rank != solver_rank:
+        return None
+    return ctx.diag(0.0, out)
