@@ -92,8 +92,9 @@ typedef struct {
     int32_t skip_validation; /* 1: trust the CSR; 0: check it on the device: row pointers, column
                                 range, self-loops, sorted rows, symmetry, isolated vertices [0] */
     int32_t graph_id;       /* fourth Philox counter word [0] */
-    int32_t block_threads;  /* threads per sampling CTA: 64, 128, 256, 512 or 1024 (the global-memory
-                               sampler of graphs above 65,535 vertices: 256 or more) [0 = by graph size] */
+    int32_t block_threads;  /* threads per sampling CTA: 32, 64, 128, 256, 512 or 1024 (the sampler of
+                               graphs above 65,535 vertices: 256 or more) [0 = tuned or by graph size,
+                               see autotune] */
     int32_t ctas_per_sm;    /* sampling CTAs per SM, capped by what registers and shared memory allow
                                [0 = as many as fit] */
     int32_t solve_fp64;     /* 1: run the whole column solve in FP64 (reference form) [0 = FP32 PCG

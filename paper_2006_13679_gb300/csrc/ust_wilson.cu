@@ -184,16 +184,16 @@ constexpr int kThreadsPerSm = 1024;
 // Graphs above kTierMaxVertices vertices: the per-tree state lives in the
 // CTA's workspace, with the hottest counter words in shared memory.
 //
-// Per vertex v of the sampler's graph, two arrays of 64-bit words:
-//   NP(v)  high 32 bits: stack depth of the current top; low 32 bits: the
-//          stack top, the tree parent at the end (-1 at u)
-//   CW(v)  by phase: (children | in-edges removed by peeling),
+// Per vertex v of the sampler's graph:
+//   NXT(v) the stack top, the tree parent at the end (-1 at u), 4 bytes
+//   DEP(v) the stack depth of the top, 4 bytes
+//   CW(v)  64 bits, by phase: (children | in-edges removed by peeling),
 //          (children | round mark), (pending children | summed sizes),
 //          (preorder number | summed sizes)
-// Kept as two plain arrays rather than one 16-byte record per vertex, the
-// next tier of hubs stays compact enough for L2 (measured: 3.5% faster on
-// R-MAT scale 22). CW words of the vertices below p.hot sit in shared
-// memory. A single graph
+// Kept as separate compact arrays (rather than one record per vertex), the
+// next tier of hubs stays in L2 (measured on R-MAT scale 22: 16-byte
+// records were 3.5% slower than 8-byte arrays). CW words of the vertices
+// below p.hot sit in shared memory. A single graph
 // is relabelled for the sampler so that these are the vertices of largest
 // degree: a uniformly drawn neighbour, and so most random successor,
 // counter and ancestor accesses, lands on them (on R-MAT scale 22 the
@@ -317,10 +317,11 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
     const int tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
-    // NP(v) at NP[v] (arrays 0, 1), CW(v) at CWg[v] (arrays 2, 3)
-    unsigned long long *NP = reinterpret_cast<unsigned long long *>(base);
-    int32_t *NP32 = base;  // NP32[2 v]: stack top / tree parent; NP32[2 v + 1]: depth / offset
-    unsigned long long *CWg = NP + S_;
+    // NXT(v): stack top, then tree parent (array 0); DEP(v): stack depth
+    // (array 1); CW(v) (arrays 2, 3, 64-bit). The successor array every walk
+    // step reads is kept at 4 bytes a vertex, compact for L2.
+    int32_t *NXT = base, *DEP = base + S_;
+    unsigned long long *CWg = reinterpret_cast<unsigned long long *>(base + 2 * S_);
     int32_t *XA = base + 4 * S_, *XB = base + 5 * S_;  // round lists, then preorder retries
     int32_t *pos = base + 6 * S_;    // index of a redrawn vertex in the round's list
     int32_t *Sx = base + 7 * S_;     // S(x) as an index into the round's list, -1 = reaches u
@@ -390,7 +391,8 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 if (v < n) {
-                    NP[v] = (unsigned long long)(uint32_t)y[k];
+                    NXT[v] = y[k];
+                    DEP[v] = 0;
                     if (y[k] >= 0 && y[k] != u) atomicAdd(W.w(checked_vertex(y[k], n, u, 1, p)), kChild);  // u's counters are never needed
                 }
             }
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             if (tid == 0) s_qh = 0;
             for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
                 const bool leaf = v < n && v != u && (*W.w(v) >> 32) == 0ull;
-                const int y0 = leaf ? checked_vertex(NP32[2ll * v], n, u, 2, p) : u;
+                const int y0 = leaf ? checked_vertex(NXT[v], n, u, 2, p) : u;
                 warp_append_capped(leaf && y0 != u, y0, Q, &s_qn, n);
             }
             __syncthreads();
@@ -434,9 +436,15 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     ny[k] = u;
                     if (y[k] != u) {
                         old[k] = atomicAdd(W.w(y[k]), 1ull);
-                        ny[k] = checked_vertex(NP32[2ll * y[k]], n, u, 3, p);
                     }
                 }
+                // y's successor only once y is peeled: a read for every step,
+                // whether or not the walk goes on, cost 38% more time on R-MAT
+                // scale 22 than the extra round trip of the steps that do
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k)
+                    if (y[k] != u && (uint32_t)old[k] + 1u == (uint32_t)(old[k] >> 32))
+                        ny[k] = checked_vertex(NXT[y[k]], n, u, 3, p);
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
@@ -493,11 +501,11 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             for (int i = tid; i < nX; i += BT) {
                 const int x = checked_vertex(X[i], n, u, 4, p);
                 if (x == u) continue;
-                const unsigned long long wx = NP[x];
-                const uint32_t k = (uint32_t)(wx >> 32) + 1u;
-                const int old = checked_vertex((int)(uint32_t)wx, n, u, 5, p);
+                const uint32_t k = (uint32_t)DEP[x] + 1u;
+                const int old = checked_vertex(NXT[x], n, u, 5, p);
                 const int y = checked_vertex(stack_entry_of(gd, p.key0, p.key1, x, orig_of(gd, x), k, tree), n, u, 5, p);
-                NP[x] = ((unsigned long long)k << 32) | (uint32_t)y;
+                NXT[x] = y;
+                DEP[x] = (int)k;
                 *W.lo(x) = (uint32_t)rounds;
                 pos[x] = i;
                 if (old != u) atomicAdd(W.hi(old), 0xFFFFFFFFu);  // one child less
@@ -516,11 +524,11 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             //     the mark, block fence), resolved after the barrier
             const int vis = -2 - rounds;
             for (int i = tid; i < nX; i += BT) {
-                int y = checked_vertex(NP32[2ll * checked_vertex(X[i], n, u, 6, p)], n, u, 6, p);
+                int y = checked_vertex(NXT[checked_vertex(X[i], n, u, 6, p)], n, u, 6, p);
                 int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = (int)*W.lo(y);
-                    const int ny = NP32[2ll * y];  // checked below, before it is used
+                    const int ny = NXT[y];  // checked below, before it is used
                     if (m == kFinal) {
                         res = -1;
                         break;
@@ -574,13 +582,13 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     const int len = wlen[i];
                     *W.lo(y) = (uint32_t)kFinal;
                     for (int k = 0; k < len; ++k) {
-                        y = checked_vertex(NP32[2ll * y], n, u, 8, p);
+                        y = checked_vertex(NXT[y], n, u, 8, p);
                         *W.lo(y) = (uint32_t)kFinal;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
                         Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
-                        y = checked_vertex(max(NP32[2ll * y], 0), n, u, 8, p);  // -1 at u: an inconsistent walk stays in the arrays
+                        y = checked_vertex(max(NXT[y], 0), n, u, 8, p);  // -1 at u: an inconsistent walk stays in the arrays
                         if ((int)*W.lo(y) == rounds) break;
                     }
                     if ((int)*W.lo(y) != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
@@ -610,7 +618,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 if (v == u) continue;
                 const int o = orig_of(gd, v);
                 const int b = __ldg(gd.rp + v), e = __ldg(gd.rp + v + 1);
-                const uint32_t k = (uint32_t)(NP[v] >> 32);
+                const uint32_t k = (uint32_t)DEP[v];
                 const unsigned long long x = philox_x64((uint32_t)o, k, tree, gd.graph, p.key0, p.key1);
                 const long long row = gd.rp_in ? (long long)__ldg(gd.rp_in + o) : (long long)b;  // input arc index
                 atomicAdd(p.edge_counts + gd.aoff + row + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
@@ -619,11 +627,10 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         if (p.mode == 1) {  // export the tree in input ids
             const long long ob = s_tree * (long long)n;
             for (int v = tid; v < n; v += BT) {
-                const unsigned long long w = NP[v];
                 const int o = orig_of(gd, v);
-                const int tp = (int)(uint32_t)w;
+                const int tp = NXT[v];
                 p.next_out[ob + o] = (tp < 0) ? -1 : orig_of(gd, tp);
-                if (p.pops_out) p.pops_out[ob + o] = (int)(w >> 32);
+                if (p.pops_out) p.pops_out[ob + o] = DEP[v];
             }
             __syncthreads();
             continue;
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             unsigned long long *Q2 = reinterpret_cast<unsigned long long *>(XA);
             for (int v = tid; v - (tid & 31) < n; v += BT) {  // uniform per warp
                 const bool leaf = v < n && v != u && *W.w(v) == 0ull;
-                const int pv = leaf ? checked_vertex(NP32[2ll * v], n, u, 9, p) : u;
+                const int pv = leaf ? checked_vertex(NXT[v], n, u, 9, p) : u;
                 warp_append_pair(leaf, ((unsigned long long)(uint32_t)v << 32) | (uint32_t)pv, Q2, &s_cnt, n);
             }
             __syncthreads();
@@ -679,9 +686,13 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     gp[k] = -1;
                     if (par[k] >= 0) {
                         old[k] = atomicAdd(W.w(par[k]), (unsigned long long)carry[k] - kChild);
-                        if (par[k] != u) gp[k] = checked_vertex(NP32[2ll * par[k]], n, u, 10, p);
                     }
                 }
+                // the parent's parent only for the last arriver, which goes on
+#pragma unroll
+                for (int k = 0; k < kWalks; ++k)
+                    if (par[k] >= 0 && par[k] != u && (old[k] >> 32) == 1ull)
+                        gp[k] = checked_vertex(NXT[par[k]], n, u, 10, p);
                 // log every arrival: x, its parent and its offset inside the
                 // parent's interval (all lanes call)
 #pragma unroll
@@ -876,7 +887,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 s0[k] = ok ? __ldg(gd.pathptr + o) : 0;
                 d[k] = ok ? __ldg(gd.pathptr + o + 1) - s0[k] : 0;
                 prev[k] = v;
-                nprev[k] = ok ? NP32[2ll * v] : -2;
+                nprev[k] = ok ? NXT[v] : -2;
                 pv[k] = ok ? *W.hi(v) : 0u;
                 cnt[k] = 0;
                 dmax = max(dmax, d[k]);
@@ -895,7 +906,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 for (int k = 0; k < kWalks; ++k)
 #pragma unroll
                     for (int j = 0; j < kAlg2Chunk; ++j)
-                        na[k][j] = (a[k][j] >= 0 && a[k][j] != u) ? NP32[2ll * a[k][j]] : -1;
+                        na[k][j] = (a[k][j] >= 0 && a[k][j] != u) ? NXT[a[k][j]] : -1;
                 int tx[kWalks][kAlg2Chunk];
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
@@ -1698,6 +1709,7 @@ cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 cudaError_t launch_shape(const LaunchCfg &cfg, int grid, cudaStream_t st, const SampleParams &p)
 {
     switch (cfg.bt) {
+    case 32: return launch_sampler<32>(grid, st, p);
     case 64: return launch_sampler<64>(grid, st, p);
     case 128: return launch_sampler<128>(grid, st, p);
     case 256: return launch_sampler<256>(grid, st, p);
@@ -1749,6 +1761,7 @@ int resident_ctas(int max_n)
 int resident_ctas_for(int bt, int max_n)
 {
     switch (bt) {
+    case 32: return resident_ctas<32>(max_n);
     case 64: return resident_ctas<64>(max_n);
     case 128: return resident_ctas<128>(max_n);
     case 256: return resident_ctas<256>(max_n);
@@ -1770,7 +1783,7 @@ int default_bt(int max_n)
     return 1024;
 }
 
-bool valid_bt(int bt) { return bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
+bool valid_bt(int bt) { return bt == 32 || bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
 
 int choose_cfg(Ctx *c, int max_n, int req_bt, int req_cps, LaunchCfg *out)
 {
@@ -1850,7 +1863,7 @@ std::map<TuneKey, LaunchCfg> g_tune_cache;
 std::vector<LaunchCfg> tune_candidates(int num_sms, int max_n)
 {
     std::vector<LaunchCfg> out;
-    for (int bt : {64, 128, 256, 512, 1024}) {
+    for (int bt : {32, 64, 128, 256, 512, 1024}) {
         if (max_n > kTierMaxVertices && bt < 512) continue;  // the large-graph sampler needs its hot words
         const int res = resident_ctas_for(bt, max_n);
         if (res < 1) continue;
