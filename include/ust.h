@@ -92,7 +92,7 @@ typedef struct {
     int32_t skip_validation; /* 1: trust the CSR; 0: check it on the device: row pointers, column
                                 range, self-loops, sorted rows, symmetry, isolated vertices [0] */
     int32_t graph_id;       /* fourth Philox counter word [0] */
-    int32_t block_threads;  /* threads per sampling CTA: 32, 64, 128, 256, 512 or 1024 (the sampler of
+    int32_t block_threads;  /* threads per sampling CTA: 64, 128, 256, 512 or 1024 (the sampler of
                                graphs above 65,535 vertices: 256 or more) [0 = tuned or by graph size,
                                see autotune] */
     int32_t ctas_per_sm;    /* sampling CTAs per SM, capped by what registers and shared memory allow
@@ -110,9 +110,7 @@ typedef struct {
                                Single-graph contexts only (ust_init_batch: UST_EINVAL)
                                [0 = plain Wilson rooted at u] */
     int32_t autotune;       /* launch shapes of the sampler: 1 = tuned, -1 = fixed table, 0 = default
-                               [tuned for ust_init_batch and for single graphs of at most 65,535
-                               vertices, fixed above (the large-graph sampler keeps 1,024 threads,
-                               the most shared memory for its hot words)]. Tuning times every
+                               [tuned for ust_init_batch, fixed table for ust_init]. Tuning times every
                                candidate shape (threads per CTA x CTAs per SM that fit) on a probe of
                                the launch's own work at context creation and keeps the fastest; the
                                choice is remembered for the process per workload key (kernel, size

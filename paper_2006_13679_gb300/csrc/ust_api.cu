@@ -194,9 +194,7 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
         if (rc) return rc;
     }
     int bt = op.block_threads, cps = op.ctas_per_sm;
-    // tuned by default below 65,536 vertices, where the probes are cheap
-    const bool tune = op.autotune > 0 || (op.autotune == 0 && n <= ust::kTierMaxVertices);
-    if (tune && bt == 0 && cps == 0 && !c->blocks) {
+    if (op.autotune > 0 && bt == 0 && cps == 0 && !c->blocks) {
         rc = tune_single(c, &bt, &cps);
         if (rc) return rc;
     }

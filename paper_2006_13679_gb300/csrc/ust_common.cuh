@@ -56,7 +56,7 @@ constexpr int kSmemMaxVertices = 56 * 1024;
 // per-CTA tail in global memory.
 constexpr int kTierMaxVertices = 0xFFFF;
 
-// One sampler launch shape: threads per CTA (32, 64, 128, 256, 512 or 1024) and
+// One sampler launch shape: threads per CTA (64, 128, 256, 512 or 1024) and
 // the persistent CTAs of the launch (a multiple of the SM count).
 struct LaunchCfg {
     int bt = 0;

@@ -232,6 +232,8 @@ struct LargeWords {
 // rounds a warp waits for the parents of deferred vertices before leaving
 // them to the next pass.
 constexpr int kPreChunkPerThread = 8;
+// Marks a leaf's entry in the arrival log (its offset field; offsets < 2^31).
+constexpr int32_t kLeafBit = (int32_t)0x80000000u;
 // Algorithm 2 entries per vertex loaded together in the large-graph sampler.
 constexpr int kAlg2Chunk = 2;
 constexpr uint32_t kPreTag = 0x80000000u;      // high word of a vertex of the current chunk
@@ -697,7 +699,9 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 // parent's interval (all lanes call)
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k)
-                    warp_log_arrival(par[k] >= 0, x[k], par[k], 1 + (int)(uint32_t)old[k], ord, ordp, ordo, &s_qn, n);
+                    warp_log_arrival(par[k] >= 0, x[k], par[k],
+                                     (1 + (int)(uint32_t)old[k]) | (carry[k] == 1u ? kLeafBit : 0), ord, ordp, ordo,
+                                     &s_qn, n);
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
@@ -753,8 +757,10 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             __syncthreads();
             for (int c0 = 0; c0 < total; c0 += K) {
                 const int len = min(K, total - c0);
-                for (int i = tid; i < len; i += BT) {
-                    const int x = checked_vertex(ord[total - 1 - (c0 + i)], n, u, 11, p);
+                for (int i = tid; i < len; i += BT) {  // leaves are nobody's parent: no tag
+                    const int j = total - 1 - (c0 + i);
+                    if (ordo[j] & kLeafBit) continue;
+                    const int x = checked_vertex(ord[j], n, u, 11, p);
                     *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = kPreTag | (uint32_t)i;
                 }
                 __syncthreads();
@@ -765,7 +771,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     for (int k = 0; k < kWalks; ++k) {
                         const int i = i0 + k * BT, j = total - 1 - (c0 + i);
                         par[k] = (i < len) ? checked_vertex(ordp[j], n, u, 13, p) : u;
-                        off[k] = (i < len) ? (uint32_t)ordo[j] : 0u;
+                        off[k] = (i < len) ? (uint32_t)(ordo[j] & ~kLeafBit) : 0u;
                     }
 #pragma unroll
                     for (int k = 0; k < kWalks; ++k)
@@ -837,7 +843,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     const bool valid = (unsigned)j < (unsigned)total;
                     const int x = valid ? checked_vertex(ord[j], n, u, 11, p) : -1;
                     const int par = valid ? checked_vertex(ordp[j], n, u, 13, p) : u;
-                    const uint32_t off = valid ? (uint32_t)ordo[j] : 0u;
+                    const uint32_t off = valid ? (uint32_t)(ordo[j] & ~kLeafBit) : 0u;
                     uint32_t pp = 0u;
                     bool ok = !valid || par == u, written = !valid;
                     // the warp waits together, so a parent numbered by another
@@ -1709,7 +1715,6 @@ cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 cudaError_t launch_shape(const LaunchCfg &cfg, int grid, cudaStream_t st, const SampleParams &p)
 {
     switch (cfg.bt) {
-    case 32: return launch_sampler<32>(grid, st, p);
     case 64: return launch_sampler<64>(grid, st, p);
     case 128: return launch_sampler<128>(grid, st, p);
     case 256: return launch_sampler<256>(grid, st, p);
@@ -1761,7 +1766,6 @@ int resident_ctas(int max_n)
 int resident_ctas_for(int bt, int max_n)
 {
     switch (bt) {
-    case 32: return resident_ctas<32>(max_n);
     case 64: return resident_ctas<64>(max_n);
     case 128: return resident_ctas<128>(max_n);
     case 256: return resident_ctas<256>(max_n);
@@ -1783,7 +1787,7 @@ int default_bt(int max_n)
     return 1024;
 }
 
-bool valid_bt(int bt) { return bt == 32 || bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
+bool valid_bt(int bt) { return bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024; }
 
 int choose_cfg(Ctx *c, int max_n, int req_bt, int req_cps, LaunchCfg *out)
 {
@@ -1863,7 +1867,7 @@ std::map<TuneKey, LaunchCfg> g_tune_cache;
 std::vector<LaunchCfg> tune_candidates(int num_sms, int max_n)
 {
     std::vector<LaunchCfg> out;
-    for (int bt : {32, 64, 128, 256, 512, 1024}) {
+    for (int bt : {64, 128, 256, 512, 1024}) {
         if (max_n > kTierMaxVertices && bt < 512) continue;  // the large-graph sampler needs its hot words
         const int res = resident_ctas_for(bt, max_n);
         if (res < 1) continue;

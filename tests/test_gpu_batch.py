@@ -142,7 +142,7 @@ def test_tuned_and_fixed_launch_shapes_give_equal_counts(pkg, orc):
         b.sample_aggregate(50, 3)
         assert np.array_equal(a.counts(), b.counts())
         shapes = {(a.graph_info(i)["sample_threads"], a.graph_info(i)["sample_ctas"]) for i in range(len(gs))}
-        assert all(bt in (32, 64, 128, 256, 512, 1024) and ctas > 0 for bt, ctas in shapes)
+        assert all(bt in (64, 128, 256, 512, 1024) and ctas > 0 for bt, ctas in shapes)
     g = synth.er(9000, 10.0, seed=7)
     u = synth.max_degree_vertex(g)
     with pkg.UST(g.row_ptr, g.col_idx, u, autotune=1) as h:

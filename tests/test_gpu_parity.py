@@ -132,7 +132,7 @@ def test_edge_graphs(pkg, orc, maker, u):
             assert np.array_equal(h.counts(), 301 * dist.astype(np.int64))
 
 
-@pytest.mark.parametrize("bt,cps", [(32, 0), (64, 0), (128, 0), (256, 1), (256, 8), (512, 2), (1024, 1)])
+@pytest.mark.parametrize("bt,cps", [(64, 0), (128, 0), (256, 1), (256, 8), (512, 2), (1024, 1)])
 def test_launch_configurations_agree(pkg, orc, bt, cps):
     g, u = GRAPHS["rmat12"]()
     with make(pkg, g, u, block_threads=bt, ctas_per_sm=cps) as h:
