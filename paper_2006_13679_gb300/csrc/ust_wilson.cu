@@ -206,8 +206,10 @@ constexpr int kThreadsPerSm = 1024;
 //  2. round 0: in-degree peeling; each step removes one in-edge of y with
 //     one atomic on CW[y] (low word) that also says whether y is now a leaf;
 //  3. the vertices left with in-edges lie on cycles: the first round list;
-//  4. popping rounds as in the shared-memory sampler, marks in the low words,
-//     children counts kept up to date in the high words;
+//  4. popping rounds as in the shared-memory sampler, marks in the low words
+//     of hot vertices and a 4-byte array for the others (compact for the
+//     long walks of round-heavy graphs), children counts kept up to date in
+//     the high words;
 //  5. subtree sizes and offsets by last arrivers; every arrival (vertex,
 //     parent, offset) is logged, so the log lists each vertex before its
 //     parent;
@@ -221,10 +223,13 @@ constexpr int kThreadsPerSm = 1024;
 struct LargeWords {
     unsigned long long *s;  // shared: the words of vertices below hot
     unsigned long long *g;  // global: CW of vertex v at g[v] (slots below hot unused)
+    uint32_t *mk;           // global: round marks of the vertices from hot on
     int hot;
     __device__ __forceinline__ unsigned long long *w(int v) const { return v < hot ? s + v : g + v; }
     __device__ __forceinline__ uint32_t *lo(int v) const { return reinterpret_cast<uint32_t *>(w(v)); }
     __device__ __forceinline__ uint32_t *hi(int v) const { return reinterpret_cast<uint32_t *>(w(v)) + 1; }
+    // round mark: the low word of a hot vertex, a 4-byte array for the others
+    __device__ __forceinline__ uint32_t *mark(int v) const { return v < hot ? lo(v) : mk + v; }
 };
 
 // Preorder phase: vertices per chunk and thread (a packed word each in the
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         if (!item_graph(p, s_tree, gd, t)) break;
         const int n = gd.n, u = gd.u;
         const uint32_t tree = (uint32_t)t;
-        const LargeWords W{s_hot, CWg, min(p.hot, n)};
+        const LargeWords W{s_hot, CWg, reinterpret_cast<uint32_t *>(ordp), min(p.hot, n)};
         if (tid == 0) {
             tmark = clock64();
             s_draws = (unsigned long long)(n - 1);
@@ -475,10 +480,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             if (v < n) {
                 const unsigned long long w = *W.w(v);
                 if (v == u) {
-                    *W.lo(v) = (uint32_t)kFinal;
+                    *W.mark(v) = (uint32_t)kFinal;
                 } else {
                     on_cycle = (uint32_t)w < (uint32_t)(w >> 32);
-                    if ((uint32_t)w != 0u) *W.lo(v) = 0u;  // the low words become round marks
+                    // the round marks: a hot vertex's low word, else the mark array
+                    if (v >= W.hot)
+                        W.mk[v] = 0u;
+                    else if ((uint32_t)w != 0u)
+                        *W.lo(v) = 0u;
                 }
             }
             warp_append_capped(on_cycle, v, XA, &s_cnt, n);
@@ -508,7 +517,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 const int y = checked_vertex(stack_entry_of(gd, p.key0, p.key1, x, orig_of(gd, x), k, tree), n, u, 5, p);
                 NXT[x] = y;
                 DEP[x] = (int)k;
-                *W.lo(x) = (uint32_t)rounds;
+                *W.mark(x) = (uint32_t)rounds;
                 pos[x] = i;
                 if (old != u) atomicAdd(W.hi(old), 0xFFFFFFFFu);  // one child less
                 if (y != u) atomicAdd(W.hi(y), 1u);
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 int y = checked_vertex(NXT[checked_vertex(X[i], n, u, 6, p)], n, u, 6, p);
                 int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
-                    const int m = (int)*W.lo(y);
+                    const int m = (int)*W.mark(y);
                     const int ny = NXT[y];  // checked below, before it is used
                     if (m == kFinal) {
                         res = -1;
@@ -547,7 +556,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     }
                     owner[y] = i;
                     __threadfence_block();  // the owner is visible before the mark
-                    *W.lo(y) = (uint32_t)vis;
+                    *W.mark(y) = (uint32_t)vis;
                     ++len;
                     y = checked_vertex(ny, n, u, 7, p);
                 }
@@ -582,18 +591,18 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 int y = checked_vertex(X[i], n, u, 8, p);
                 if (kind == 1) {
                     const int len = wlen[i];
-                    *W.lo(y) = (uint32_t)kFinal;
+                    *W.mark(y) = (uint32_t)kFinal;
                     for (int k = 0; k < len; ++k) {
                         y = checked_vertex(NXT[y], n, u, 8, p);
-                        *W.lo(y) = (uint32_t)kFinal;
+                        *W.mark(y) = (uint32_t)kFinal;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
                         Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
                         y = checked_vertex(max(NXT[y], 0), n, u, 8, p);  // -1 at u: an inconsistent walk stays in the arrays
-                        if ((int)*W.lo(y) == rounds) break;
+                        if ((int)*W.mark(y) == rounds) break;
                     }
-                    if ((int)*W.lo(y) != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
+                    if ((int)*W.mark(y) != rounds) s_err = 1;  // a cycle segment ends at a redrawn vertex
                 }
             }
             __syncthreads();
@@ -637,7 +646,8 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             __syncthreads();
             continue;
         }
-        // the low words sum subtree sizes from now on
+        // the low words sum subtree sizes from now on (they still hold round
+        // marks of hot vertices and peeling's removed in-edges of the others)
         for (int v = tid; v < n; v += BT)
             if (*W.lo(v) != 0u) *W.lo(v) = 0u;
         if (tid == 0) {
