@@ -145,12 +145,14 @@ typedef struct {
     int64_t last_trees;     /* trees processed by the last sampling launch */
     int64_t last_draws;     /* stack entries drawn by the last sampling launch */
     /* SM clock cycles of the last sampling launch per phase, summed over
-     * trees (graphs of at most 56k vertices): [0] first draws, [1] in-degrees,
-     * [2] leaf queue, [3] peeling, [4] cycle list, [5] later popping rounds,
-     * [6] children counts and leaf queue, [7] subtree sizes and offsets,
-     * [8] preorder numbers, [9] Algorithm 2, [10] whole tree, [11] unused.
-     * Larger graphs fill [0] first draws, [1] in-degrees, [2] peeling,
-     * [3] rounds, [4] sizes, [5] preorder, [6] Algorithm 2, [7] whole tree. */
+     * trees (graphs of at most 65,535 vertices): [0] first draws,
+     * [1] in-degrees, [2] leaf queue, [3] peeling, [4] cycle list, [5] later
+     * popping rounds, [6] children counts and leaf queue, [7] subtree sizes
+     * and offsets, [8] preorder numbers, [9] Algorithm 2, [10] whole tree,
+     * [11] unused. Larger graphs fill [0] first draws and in-degrees,
+     * [1] peeling, [2] cycle list, [3] later popping rounds, [4] subtree
+     * sizes and offsets, [5] preorder numbers, [6] Algorithm 2, [7] whole
+     * tree; [8] to [11] unused. */
     int64_t last_phase_cycles[12];
 } ust_info;
 

@@ -150,7 +150,7 @@ struct Ctx {
 
     // The large-graph sampler's view of a single graph above
     // kTierMaxVertices vertices (plain Wilson): vertex ids relabelled so
-    // that the kLargeHotMax highest-degree vertices come first (by degree,
+    // that the kRelabelTop highest-degree vertices come first (by degree,
     // then id) and the rest follow in input order; every row keeps its
     // input order. B_u, the solve and all outputs stay in input ids.
     bool relabel = false;
@@ -260,10 +260,10 @@ inline void phase_close(Ctx *c, int ph)
 
 // Host drivers (one per translation unit).
 int run_bfs(Ctx *c);
-// Vertices whose counter words the large-graph sampler keeps in shared
-// memory at most (1024 threads, one CTA per SM); the relabelling puts the
-// highest-degree vertices below this id.
-constexpr int kLargeHotMax = 28 * 1024;
+// Vertices the large-graph sampler's relabelling moves to the front, in
+// order of decreasing degree (their per-vertex entries then share cache
+// lines in L1 and L2).
+constexpr int kRelabelTop = 28 * 1024;
 // The relabelled CSR of the large-graph sampler (ust_relabel.cu), built once
 // per context, and its flattened BFS paths, rebuilt with every B_u.
 int build_relabel(Ctx *c);

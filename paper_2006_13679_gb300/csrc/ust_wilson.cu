@@ -93,7 +93,6 @@ struct SampleParams {
     int32_t *next_out, *pops_out;  // mode 1: item i's tree at [i n, (i + 1) n)
     unsigned long long *edge_counts;  // when set: +1 per tree at every arc v -> parent(v) (index aoff + arc)
     unsigned long long *R_direct;   // when set, counts go to R_direct[voff + v] (batches)
-    int hot;  // large-graph sampler: vertices whose counter words sit in shared memory
 };
 
 // item_start[1] of a one-graph launch: its items end at total_items.
@@ -182,7 +181,7 @@ constexpr int kThreadsPerSm = 1024;
 
 // ---------------------------------------------------------------------------
 // Graphs above kTierMaxVertices vertices: the per-tree state lives in the
-// CTA's workspace, with the hottest counter words in shared memory.
+// CTA's workspace, in global memory, cached by L1 and L2.
 //
 // Per vertex v of the sampler's graph:
 //   NXT(v) the stack top, the tree parent at the end (-1 at u), 4 bytes
@@ -190,26 +189,30 @@ constexpr int kThreadsPerSm = 1024;
 //   CW(v)  64 bits, by phase: (children | in-edges removed by peeling),
 //          (children | round mark), (pending children | summed sizes),
 //          (preorder number | summed sizes)
+//   MK(v)  the round mark of the popping rounds, 4 bytes
 // Kept as separate compact arrays (rather than one record per vertex), the
-// next tier of hubs stays in L2 (measured on R-MAT scale 22: 16-byte
-// records were 3.5% slower than 8-byte arrays). CW words of the vertices
-// below p.hot sit in shared memory. A single graph
-// is relabelled for the sampler so that these are the vertices of largest
-// degree: a uniformly drawn neighbour, and so most random successor,
-// counter and ancestor accesses, lands on them (on R-MAT scale 22 the
-// 28,672 highest-degree vertices, 1.2% of them, take 55% of the first
-// draws). The relabelling keeps every row in the input order and every
-// draw keyed by the input id (gd.orig), so the trees are unchanged.
+// hubs' entries stay in L1 and L2 (measured on R-MAT scale 22: 16-byte
+// records were 3.5% slower than 8-byte arrays). Nothing of a tree sits in
+// shared memory: the kernel leaves the SM's whole 256 KB to L1, which holds
+// the hubs' entries (measured: keeping the CW words of the 28,672 vertices
+// of largest degree in shared memory instead was 14% slower on R-MAT scale
+// 22 and 22% slower on a 2^20-vertex hyperbolic graph). A single graph is
+// relabelled for the sampler so that the vertices of largest degree come
+// first, their entries side by side in few cache lines: a uniformly drawn
+// neighbour, and so most random successor, counter and ancestor accesses,
+// lands on them (on R-MAT scale 22 the 28,672 highest-degree vertices, 1.2%
+// of them, take 55% of the first draws). The relabelling keeps every row in
+// the input order and every draw keyed by the input id (gd.orig), so the
+// trees are unchanged.
 //
 // Phases per tree (one CTA per tree, CTA barriers only):
 //  1. first draws, in-degrees into CW (high words);
 //  2. round 0: in-degree peeling; each step removes one in-edge of y with
 //     one atomic on CW[y] (low word) that also says whether y is now a leaf;
 //  3. the vertices left with in-edges lie on cycles: the first round list;
-//  4. popping rounds as in the shared-memory sampler, marks in the low words
-//     of hot vertices and a 4-byte array for the others (compact for the
-//     long walks of round-heavy graphs), children counts kept up to date in
-//     the high words;
+//  4. popping rounds as in the shared-memory sampler, marks in MK (compact
+//     for the long walks of round-heavy graphs), children counts kept up to
+//     date in the high words of CW;
 //  5. subtree sizes and offsets by last arrivers; every arrival (vertex,
 //     parent, offset) is logged, so the log lists each vertex before its
 //     parent;
@@ -221,15 +224,12 @@ constexpr int kThreadsPerSm = 1024;
 //     (bfs_parent(v), v) needs no interval (v lies in its own subtree, and
 //     never below its own tree child).
 struct LargeWords {
-    unsigned long long *s;  // shared: the words of vertices below hot
-    unsigned long long *g;  // global: CW of vertex v at g[v] (slots below hot unused)
-    uint32_t *mk;           // global: round marks of the vertices from hot on
-    int hot;
-    __device__ __forceinline__ unsigned long long *w(int v) const { return v < hot ? s + v : g + v; }
-    __device__ __forceinline__ uint32_t *lo(int v) const { return reinterpret_cast<uint32_t *>(w(v)); }
-    __device__ __forceinline__ uint32_t *hi(int v) const { return reinterpret_cast<uint32_t *>(w(v)) + 1; }
-    // round mark: the low word of a hot vertex, a 4-byte array for the others
-    __device__ __forceinline__ uint32_t *mark(int v) const { return v < hot ? lo(v) : mk + v; }
+    unsigned long long *g;  // CW of vertex v at g[v]
+    uint32_t *mk;           // MK of vertex v at mk[v]
+    __device__ __forceinline__ unsigned long long *w(int v) const { return g + v; }
+    __device__ __forceinline__ uint32_t *lo(int v) const { return reinterpret_cast<uint32_t *>(g + v); }
+    __device__ __forceinline__ uint32_t *hi(int v) const { return reinterpret_cast<uint32_t *>(g + v) + 1; }
+    __device__ __forceinline__ uint32_t *mark(int v) const { return mk + v; }
 };
 
 // Preorder phase: vertices per chunk and thread (a packed word each in the
@@ -320,7 +320,6 @@ __device__ __forceinline__ void warp_append_pair(bool flag, unsigned long long v
 template <int BT>
 __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large_kernel(SampleParams p)
 {
-    extern __shared__ unsigned long long s_hot[];
     const int tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
@@ -365,7 +364,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         if (!item_graph(p, s_tree, gd, t)) break;
         const int n = gd.n, u = gd.u;
         const uint32_t tree = (uint32_t)t;
-        const LargeWords W{s_hot, CWg, reinterpret_cast<uint32_t *>(ordp), min(p.hot, n)};
+        const LargeWords W{CWg, reinterpret_cast<uint32_t *>(ordp)};
         if (tid == 0) {
             tmark = clock64();
             s_draws = (unsigned long long)(n - 1);
@@ -375,8 +374,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         }
 
         // ---- 1. first draws and in-degrees ---------------------------------
-        for (int w = tid; w < W.hot; w += BT) s_hot[w] = 0ull;
-        for (int v = W.hot + tid; v < n; v += BT) CWg[v] = 0ull;
+        for (int v = tid; v < n; v += BT) CWg[v] = 0ull;
         __syncthreads();
         for (int b0 = tid; b0 < n; b0 += BT * kWalks) {
             int o[kWalks], rb[kWalks], deg[kWalks];
@@ -483,11 +481,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                     *W.mark(v) = (uint32_t)kFinal;
                 } else {
                     on_cycle = (uint32_t)w < (uint32_t)(w >> 32);
-                    // the round marks: a hot vertex's low word, else the mark array
-                    if (v >= W.hot)
-                        W.mk[v] = 0u;
-                    else if ((uint32_t)w != 0u)
-                        *W.lo(v) = 0u;
+                    *W.mark(v) = 0u;
                 }
             }
             warp_append_capped(on_cycle, v, XA, &s_cnt, n);
@@ -646,8 +640,8 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             __syncthreads();
             continue;
         }
-        // the low words sum subtree sizes from now on (they still hold round
-        // marks of hot vertices and peeling's removed in-edges of the others)
+        // the low words sum subtree sizes from now on (they still hold
+        // peeling's removed in-edges)
         for (int v = tid; v < n; v += BT)
             if (*W.lo(v) != 0u) *W.lo(v) = 0u;
         if (tid == 0) {
@@ -1680,18 +1674,11 @@ size_t smem_bytes_for(int max_n) { return (size_t)((max_n + 1) / 2) * 2 * sizeof
 
 int64_t stride_for(int max_n) { return ((int64_t)max_n + 2 + 31) / 32 * 32; }
 
-// Counter words the large-graph sampler keeps in shared memory at BT threads
-// per CTA: as many as the CTAs that fill one SM's 228 KB leave each after
-// 1 KB reserved per CTA and the kernel's own variables.
-constexpr int large_hot_cap(int bt) { return bt >= 1024 ? kLargeHotMax : bt == 512 ? 14336 : 7040; }
-static_assert(kLargeHotMax * 8 + 1024 + 256 <= 227 * 1024, "hot words fit one CTA's shared memory");
-
-size_t large_smem_bytes(const SampleParams &p) { return (size_t)std::max(1, std::min(p.hot, p.max_n)) * 8; }
-
 // Graphs of at most kSmemMaxN vertices run the shared-memory kernel at any
 // shape; up to kTierMaxVertices the same kernel with its last words in the
 // workspace tail; larger graphs the large-graph kernel, built for 256
-// threads and more, with p.hot counter words in shared memory.
+// threads and more, with no dynamic shared memory (the SM's on-chip memory
+// goes to L1).
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
@@ -1709,12 +1696,7 @@ cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
         sample_aggregate_smem_kernel<BT, true><<<grid, BT, bytes, st>>>(p);
     } else {
         if constexpr (BT >= 256) {
-            if (p.hot > large_hot_cap(BT)) return cudaErrorInvalidValue;
-            const size_t bytes = large_smem_bytes(p);
-            cudaError_t e = cudaFuncSetAttribute(sample_aggregate_large_kernel<BT>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-            if (e != cudaSuccess) return e;
-            sample_aggregate_large_kernel<BT><<<grid, BT, bytes, st>>>(p);
+            sample_aggregate_large_kernel<BT><<<grid, BT, 0, st>>>(p);
         } else {
             return cudaErrorInvalidConfiguration;
         }
@@ -1758,14 +1740,7 @@ int resident_ctas(int max_n)
             return 0;
     } else {
         if constexpr (BT >= 256) {
-            SampleParams q{};
-            q.max_n = max_n;
-            q.hot = large_hot_cap(BT);
-            const size_t bytes = large_smem_bytes(q);
-            if (cudaFuncSetAttribute(sample_aggregate_large_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)bytes) != cudaSuccess)
-                return 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_large_kernel<BT>, BT, bytes) !=
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_large_kernel<BT>, BT, 0) !=
                 cudaSuccess)
                 return 0;
         }
@@ -1792,8 +1767,11 @@ int default_bt(int max_n)
     if (max_n <= 8192) return 128;
     if (max_n <= 14336) return 256;
     if (max_n <= 28672) return 512;
-    // above: one whole-SM tree per SM, which leaves the most shared memory
-    // for the hot counter words of the large-graph sampler
+    // above: one whole-SM tree per SM; the large-graph sampler's trees are
+    // bound by their dependent chains, which 1,024 threads shorten most
+    // (measured on R-MAT scale 22: 512 x 2 is 8% and 256 x 4 17% slower; a
+    // 2^20-vertex hyperbolic graph, with its many popping rounds, gains 7%
+    // at 512 x 2, which the launch-shape tuner finds)
     return 1024;
 }
 
@@ -1878,7 +1856,7 @@ std::vector<LaunchCfg> tune_candidates(int num_sms, int max_n)
 {
     std::vector<LaunchCfg> out;
     for (int bt : {64, 128, 256, 512, 1024}) {
-        if (max_n > kTierMaxVertices && bt < 512) continue;  // the large-graph sampler needs its hot words
+        if (max_n > kTierMaxVertices && bt < 512) continue;  // slower in every measured large-graph case
         const int res = resident_ctas_for(bt, max_n);
         if (res < 1) continue;
         out.push_back(LaunchCfg{bt, num_sms * res});
@@ -1915,7 +1893,6 @@ int probe_launch(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, const 
     p.max_steps = lg + 4;
     p.mode = 0;
     p.R_direct = reinterpret_cast<unsigned long long *>(d_scratch);
-    p.hot = large_hot_cap(cfg.bt);
     const int grid = (int)std::min<long long>(cfg.ctas, items);
     if ((int64_t)grid * kWsArrays * p.stride > c->ws_cap) return fail(c, UST_ECUDA, "tuning probe: workspace too small");
     cudaEvent_t e0 = c->ev[2 * Ctx::kEvSample], e1 = c->ev[2 * Ctx::kEvSample + 1];
@@ -2064,7 +2041,6 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     p.mode = mode;
     p.next_out = d_next_out;
     p.pops_out = d_pops_out;
-    p.hot = large_hot_cap(c->cfg.bt);
 
     phase_begin(c, Ctx::kEvSample);
     const cudaError_t e = launch_shape(c->cfg, grid, c->stream, p);
@@ -2458,7 +2434,6 @@ int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, c
     p.total_items = total_items;
     p.R_direct = reinterpret_cast<unsigned long long *>(d_R);
     p.edge_counts = reinterpret_cast<unsigned long long *>(c->d_ecount_tmp);
-    p.hot = large_hot_cap(cfg.bt);
     const int grid = (int)std::min<long long>(cfg.ctas, total_items);
     phase_begin(c, Ctx::kEvSample);
     const cudaError_t e = launch_shape(cfg, grid, c->stream, p);
