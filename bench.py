@@ -38,8 +38,10 @@ METRIC = "USTs sampled+aggregated/sec and diag(L†) wall time on 1 GB300; % of 
 SEED = 0
 # DRAM traffic of the sampler from ncu captures of the sampler kernel: bytes per
 # vertex-tree of the captured launch, the workloads it is scaled to, and the sha1 of
-# csrc/ust_wilson.cu when it was taken.
+# the sampler's sources (the kernel and the relabelling that orders its memory) when
+# it was taken.
 TRAFFIC_CAPTURES = []
+SAMPLER_SOURCES = ("ust_wilson.cu", "ust_relabel.cu")
 
 # workload -> (description, oracle sample in trees for the CPU baseline; None = all)
 WORKLOADS = {
@@ -97,16 +99,25 @@ def sampler_kernel(n: int) -> str:
     return "sample_aggregate_smem_kernel" if n <= 0xFFFF else "sample_aggregate_large_kernel"
 
 
+def sampler_sha1():
+    """sha1 over the sampler's sources, in SAMPLER_SOURCES order."""
+    import hashlib
+    h = hashlib.sha1()
+    try:
+        for name in SAMPLER_SOURCES:
+            h.update(open(os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", name), "rb").read())
+    except OSError:
+        return None
+    return h.hexdigest()
+
+
 def traffic_per_launch(workload: str, n: int, trees: int):
     """DRAM bytes (read + write) of one sampler launch: an ncu capture's
     dram__bytes_read.sum + dram__bytes_write.sum per vertex-tree, times this
-    launch's n x trees. A capture counts only while the sampler source hashes
-    as it did when the counters were taken; None otherwise."""
-    import hashlib
-    try:
-        src = os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", "ust_wilson.cu")
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    except OSError:
+    launch's n x trees. A capture counts only while the sampler sources hash
+    as they did when the counters were taken; None otherwise."""
+    sha = sampler_sha1()
+    if sha is None:
         return None
     for cap in TRAFFIC_CAPTURES:
         if workload in cap["applies_to"] and cap["sha1"] == sha:

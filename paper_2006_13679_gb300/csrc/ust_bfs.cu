@@ -583,6 +583,12 @@ int run_bfs_small(Ctx *c)
     return UST_OK;
 }
 
+cudaError_t launch_exclusive_scan(int n, const int32_t *in, int32_t *out, cudaStream_t st)
+{
+    path_offsets_kernel<<<1, kScanThreads, 0, st>>>(n, in, out);
+    return cudaGetLastError();
+}
+
 int run_bfs(Ctx *c)
 {
     if (c->n <= kPrepMaxN) return run_bfs_small(c);

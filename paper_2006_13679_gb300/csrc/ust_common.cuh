@@ -149,9 +149,8 @@ struct Ctx {
     bool ready = false;
 
     // The large-graph sampler's view of a single graph above
-    // kTierMaxVertices vertices (plain Wilson): vertex ids relabelled so
-    // that the kRelabelTop highest-degree vertices come first (by degree,
-    // then id) and the rest follow in input order; every row keeps its
+    // kTierMaxVertices vertices (plain Wilson): vertex ids relabelled in
+    // Cuthill-McKee order from the pivot of ust_init; every row keeps its
     // input order. B_u, the solve and all outputs stay in input ids.
     bool relabel = false;
     int32_t *d_srp = nullptr, *d_sci = nullptr;     // relabelled CSR
@@ -159,7 +158,6 @@ struct Ctx {
     int32_t *d_spath = nullptr;                     // flattened BFS paths in sampler ids
     int64_t spath_cap = 0;
     int spivot = 0;                                 // the pivot's sampler id
-    std::vector<int32_t> h_newid;
 
     // sampling
     LaunchCfg cfg;                  // single graph: the sampler's launch shape
@@ -260,10 +258,8 @@ inline void phase_close(Ctx *c, int ph)
 
 // Host drivers (one per translation unit).
 int run_bfs(Ctx *c);
-// Vertices the large-graph sampler's relabelling moves to the front, in
-// order of decreasing degree (their per-vertex entries then share cache
-// lines in L1 and L2).
-constexpr int kRelabelTop = 28 * 1024;
+// Exclusive prefix sum of in[0, n) into out[0, n] (out[n] = total), one CTA.
+cudaError_t launch_exclusive_scan(int n, const int32_t *in, int32_t *out, cudaStream_t st);
 // The relabelled CSR of the large-graph sampler (ust_relabel.cu), built once
 // per context, and its flattened BFS paths, rebuilt with every B_u.
 int build_relabel(Ctx *c);
