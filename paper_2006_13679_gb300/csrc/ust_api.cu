@@ -42,6 +42,7 @@ void release(Ctx *c)
     cudaFree(c->d_sci);
     cudaFree(c->d_orig);
     cudaFree(c->d_newid);
+    cudaFree(c->d_spathptr);
     cudaFree(c->d_spath);
     cudaFree(c->d_ws);
     cudaFree(c->d_Rp);

@@ -42,9 +42,12 @@ struct GraphDesc {
     int fc;
     long long aoff;  // offset of the graph's arcs in batch-wide arc arrays
     // Graphs relabelled for the large-graph sampler (single graphs above
-    // kTierMaxVertices): rp / ci / u / path are in sampler ids, orig[v] is
-    // the input id of sampler vertex v (Philox counters, pathptr, outputs)
+    // kTierMaxVertices): rp / ci / u / path / pathptr are in sampler ids (the
+    // path of sampler vertex v at pathptr[v], listed in sampler order),
+    // orig[v] is the input id of sampler vertex v (Philox counters, outputs)
     // and rp_in the input row_ptr (arc counts). NULL: ids are input ids.
+    // (bpar, pchild and powner stay in input ids; the large-graph sampler
+    // does not read them.)
     const int32_t *orig, *rp_in;
 };
 
@@ -155,7 +158,8 @@ struct Ctx {
     bool relabel = false;
     int32_t *d_srp = nullptr, *d_sci = nullptr;     // relabelled CSR
     int32_t *d_orig = nullptr, *d_newid = nullptr;  // sampler id -> input id, and back
-    int32_t *d_spath = nullptr;                     // flattened BFS paths in sampler ids
+    int32_t *d_spath = nullptr;                     // flattened BFS paths in sampler ids and order
+    int32_t *d_spathptr = nullptr;                  // where sampler vertex v's path starts in d_spath
     int64_t spath_cap = 0;
     int spivot = 0;                                 // the pivot's sampler id
 

@@ -216,13 +216,24 @@ __global__ void relabel_rows_kernel(int n, const int32_t *__restrict__ rp, const
     }
 }
 
-// Flattened BFS paths in sampler ids (the entry order stays the input's).
-__global__ void relabel_path_kernel(long long count, const int32_t *__restrict__ path,
+// len[v] = |P(orig[v])| = dist(orig[v])
+__global__ void spath_lengths_kernel(int n, const int32_t *__restrict__ orig, const int32_t *__restrict__ dist,
+                                     int32_t *__restrict__ len)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) len[v] = dist[orig[v]];
+}
+
+// The flattened BFS paths in sampler ids and sampler order: the path of
+// sampler vertex v at spathptr[v], its entries in the input path's order.
+__global__ void relabel_path_kernel(int n, const int32_t *__restrict__ orig, const int32_t *__restrict__ pathptr,
+                                    const int32_t *__restrict__ path, const int32_t *__restrict__ spathptr,
                                     const int32_t *__restrict__ newid, int32_t *__restrict__ spath)
 {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
-         q += (long long)gridDim.x * blockDim.x)
-        spath[q] = newid[path[q]];
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int o = orig[v];
+        const int src = pathptr[o], len = pathptr[o + 1] - src, dst = spathptr[v];
+        for (int k = 0; k < len; ++k) spath[dst + k] = newid[path[src + k]];
+    }
 }
 
 }  // namespace
@@ -233,7 +244,8 @@ int build_relabel(Ctx *c)
     if (ecc < 1 || ecc >= n) return fail(c, UST_ECUDA, "relabelling: BFS levels missing");
     if (cudaMalloc(&c->d_srp, ((size_t)n + 1) * 4) != cudaSuccess ||
         cudaMalloc(&c->d_sci, (size_t)c->nnz * 4) != cudaSuccess || cudaMalloc(&c->d_orig, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&c->d_newid, (size_t)n * 4) != cudaSuccess)
+        cudaMalloc(&c->d_newid, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&c->d_spathptr, ((size_t)n + 1) * 4) != cudaSuccess)
         return fail(c, UST_ENOMEM, "relabelled graph of the sampler");
     // scratch of the construction: two (key, value) pairs of n, the level
     // list, histogram and offsets, the level starts and a flag
@@ -338,13 +350,18 @@ int relabel_paths(Ctx *c)
             return fail(c, UST_ENOMEM, "BFS paths in sampler ids");
         c->spath_cap = c->farness;
     }
-    if (c->farness > 0) {
-        const int threads = 256;
-        const int blocks = (int)std::min<int64_t>((c->farness + threads - 1) / threads, (int64_t)c->num_sms * 8);
-        relabel_path_kernel<<<blocks, threads, 0, c->stream>>>(c->farness, c->d_path, c->d_newid, c->d_spath);
-        c->launches += 1;
-        UST_CUDA_TRY(cudaGetLastError());
-    }
+    const int n = c->n;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)c->num_sms * 8);
+    // the path lengths go through the counts scratch (n int64, free here)
+    int32_t *len = reinterpret_cast<int32_t *>(c->d_Rtmp);
+    spath_lengths_kernel<<<blocks, threads, 0, c->stream>>>(n, c->d_orig, c->d_dist, len);
+    UST_CUDA_TRY(cudaGetLastError());
+    UST_CUDA_TRY(launch_exclusive_scan(n, len, c->d_spathptr, c->stream));
+    relabel_path_kernel<<<blocks, threads, 0, c->stream>>>(n, c->d_orig, c->d_pathptr, c->d_path, c->d_spathptr,
+                                                           c->d_newid, c->d_spath);
+    c->launches += 3;
+    UST_CUDA_TRY(cudaGetLastError());
     int32_t sp = 0;
     UST_CUDA_TRY(cudaMemcpyAsync(&sp, c->d_newid + c->pivot, sizeof(sp), cudaMemcpyDeviceToHost, c->stream));
     UST_CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -232,11 +232,12 @@ struct LargeWords {
     __device__ __forceinline__ uint32_t *mark(int v) const { return mk + v; }
 };
 
-// Preorder phase: vertices per chunk and thread (a packed word each in the
-// CTA's workspace), the tag and link values of the high words, and the
-// rounds a warp waits for the parents of deferred vertices before leaving
-// them to the next pass.
+// Preorder phase: vertices per chunk and thread (a packed word each in
+// shared memory, 64 KB at 1,024 threads), the tag and link values of the
+// high words, and the rounds a warp waits for the parents of deferred
+// vertices before leaving them to the next pass.
 constexpr int kPreChunkPerThread = 8;
+constexpr int kPreBatch = 4;  // of them loaded together
 // Marks a leaf's entry in the arrival log (its offset field; offsets < 2^31).
 constexpr int32_t kLeafBit = (int32_t)0x80000000u;
 // Algorithm 2 entries per vertex loaded together in the large-graph sampler.
@@ -320,6 +321,7 @@ __device__ __forceinline__ void warp_append_pair(bool flag, unsigned long long v
 template <int BT>
 __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large_kernel(SampleParams p)
 {
+    extern __shared__ unsigned long long s_chunk[];  // preorder chunk: kPreChunkPerThread x BT words
     const int tid = threadIdx.x;
     const long long S_ = p.stride;
     int32_t *base = p.ws + (long long)blockIdx.x * kWsArrays * S_;
@@ -752,37 +754,50 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         // warp waits a bounded number of rounds for the parents; what is
         // still pending goes to the next pass.
         {
-            // the chunk's packed words in the XB array (free until the
-            // deferred passes), L2-resident
-            volatile unsigned long long *chunk = reinterpret_cast<volatile unsigned long long *>(XB);
+            // the chunk's packed words in shared memory; a thread's log
+            // entries are loaded together before any of them is used
+            volatile unsigned long long *chunk = s_chunk;
+            constexpr int C = kPreChunkPerThread;
             const int total = n - 1;
-            const int K = min(kPreChunkPerThread * BT, (int)(S_ / 2));
+            const int K = C * BT;
             if (tid == 0) s_cnt = 0;  // deferred vertices, listed in XA
             __syncthreads();
             for (int c0 = 0; c0 < total; c0 += K) {
                 const int len = min(K, total - c0);
-                for (int i = tid; i < len; i += BT) {  // leaves are nobody's parent: no tag
-                    const int j = total - 1 - (c0 + i);
-                    if (ordo[j] & kLeafBit) continue;
-                    const int x = checked_vertex(ord[j], n, u, 11, p);
-                    *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = kPreTag | (uint32_t)i;
+#pragma unroll 1
+                for (int k0 = 0; k0 < C; k0 += kPreBatch) {  // tags; leaves are nobody's parent: no tag
+                    int xs[kPreBatch];
+                    int32_t os[kPreBatch];
+#pragma unroll
+                    for (int k = 0; k < kPreBatch; ++k) {
+                        const int i = tid + (k0 + k) * BT, j = total - 1 - (c0 + i);
+                        os[k] = (i < len) ? ordo[j] : kLeafBit;
+                        xs[k] = (i < len) ? ord[j] : u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kPreBatch; ++k)
+                        if (!(os[k] & kLeafBit))
+                            *W.hi(checked_vertex(xs[k], n, u, 11, p)) = kPreTag | (uint32_t)(tid + (k0 + k) * BT);
                 }
                 __syncthreads();
-                for (int i0 = tid; i0 < len; i0 += BT * kWalks) {
-                    int par[kWalks];
-                    uint32_t off[kWalks], h[kWalks];
+                // each entry's parent: numbered, tagged or neither (the
+                // barrier makes the tags visible to plain loads)
+#pragma unroll 1
+                for (int k0 = 0; k0 < C; k0 += kPreBatch) {
+                    int par[kPreBatch];
+                    uint32_t off[kPreBatch], h[kPreBatch];
 #pragma unroll
-                    for (int k = 0; k < kWalks; ++k) {
-                        const int i = i0 + k * BT, j = total - 1 - (c0 + i);
+                    for (int k = 0; k < kPreBatch; ++k) {
+                        const int i = tid + (k0 + k) * BT, j = total - 1 - (c0 + i);
                         par[k] = (i < len) ? checked_vertex(ordp[j], n, u, 13, p) : u;
                         off[k] = (i < len) ? (uint32_t)(ordo[j] & ~kLeafBit) : 0u;
                     }
 #pragma unroll
-                    for (int k = 0; k < kWalks; ++k)
-                        h[k] = (par[k] != u) ? *reinterpret_cast<volatile uint32_t *>(W.hi(par[k])) : 0u;
+                    for (int k = 0; k < kPreBatch; ++k) h[k] = (par[k] != u) ? *W.hi(par[k]) : 0u;
 #pragma unroll
-                    for (int k = 0; k < kWalks; ++k) {
-                        if (i0 + k * BT >= len) continue;
+                    for (int k = 0; k < kPreBatch; ++k) {
+                        const int i = tid + (k0 + k) * BT;
+                        if (i >= len) continue;
                         uint32_t link = kPreRoot, sum = off[k];
                         if (par[k] != u) {
                             if (h[k] & kPreTag)
@@ -792,7 +807,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                             else
                                 link = kPreDeferred;
                         }
-                        chunk[i0 + k * BT] = ((unsigned long long)link << 32) | sum;
+                        chunk[i] = ((unsigned long long)link << 32) | sum;
                     }
                 }
                 __syncthreads();
@@ -801,7 +816,10 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 for (int step = 0;; ++step) {
                     bool any = false;
                     if (step <= 32) {
-                        for (int i = tid; i < len; i += BT) {
+#pragma unroll
+                        for (int k = 0; k < C; ++k) {
+                            const int i = tid + k * BT;
+                            if (i >= len) continue;
                             const unsigned long long a = chunk[i];
                             const uint32_t l = (uint32_t)(a >> 32);
                             if (l >= kPreRoot) continue;  // resolved or deferred
@@ -819,16 +837,27 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                         break;
                     }
                 }
-                for (int i = tid; i - (tid & 31) < len; i += BT) {  // uniform per warp
-                    bool deferred = false;
-                    const int j = total - 1 - (c0 + i);
-                    if (i < len) {
-                        const int x = checked_vertex(ord[j], n, u, 11, p);
-                        const unsigned long long a = chunk[i];
-                        deferred = (uint32_t)(a >> 32) != kPreRoot;
-                        *reinterpret_cast<volatile uint32_t *>(W.hi(x)) = deferred ? 0u : (uint32_t)a;
+#pragma unroll 1
+                for (int k0 = 0; k0 < C; k0 += kPreBatch) {  // the numbers into the high words; deferred entries listed
+                    int xs[kPreBatch];
+#pragma unroll
+                    for (int k = 0; k < kPreBatch; ++k) {
+                        const int i = tid + (k0 + k) * BT, j = total - 1 - (c0 + i);
+                        xs[k] = (i < len) ? ord[j] : u;
                     }
-                    warp_append_capped(deferred, j, XA, &s_cnt, n);  // the log position
+#pragma unroll
+                    for (int k = 0; k < kPreBatch; ++k) {
+                        const int i = tid + (k0 + k) * BT;
+                        bool deferred = false;
+                        if (i < len) {
+                            const int x = checked_vertex(xs[k], n, u, 11, p);
+                            const unsigned long long a = chunk[i];
+                            deferred = (uint32_t)(a >> 32) != kPreRoot;
+                            *W.hi(x) = deferred ? 0u : (uint32_t)a;
+                        }
+                        // i - lane < len is uniform per warp (BT is a multiple of 32)
+                        if (i - (tid & 31) < len) warp_append_capped(deferred, total - 1 - (c0 + i), XA, &s_cnt, n);
+                    }
                 }
                 __syncthreads();
             }
@@ -880,8 +909,8 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         UST_PHASE(5);
 
         // ---- 7. Algorithm 2 ------------------------------------------------------
-        // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u (input order at
-        // pathptr[o], o = v's input id; entries in sampler ids). Edge (a_j+1,
+        // P(v) = v, a_1 = bfs_parent(v), ..., a_d = u (at pathptr[v]; for a
+        // relabelled graph in sampler ids and order). Edge (a_j+1,
         // a_j) counts +1 when T uses it downwards (parent(a_j) = a_j+1) and v
         // lies in a_j's subtree, -1 when T uses it upwards and v lies in
         // a_j+1's subtree.
@@ -893,9 +922,8 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 const bool ok = v < n && v != u;
-                const int o = ok ? orig_of(gd, v) : 0;
-                s0[k] = ok ? __ldg(gd.pathptr + o) : 0;
-                d[k] = ok ? __ldg(gd.pathptr + o + 1) - s0[k] : 0;
+                s0[k] = ok ? __ldg(gd.pathptr + v) : 0;
+                d[k] = ok ? __ldg(gd.pathptr + v + 1) - s0[k] : 0;
                 prev[k] = v;
                 nprev[k] = ok ? NXT[v] : -2;
                 pv[k] = ok ? *W.hi(v) : 0u;
@@ -1674,11 +1702,14 @@ size_t smem_bytes_for(int max_n) { return (size_t)((max_n + 1) / 2) * 2 * sizeof
 
 int64_t stride_for(int max_n) { return ((int64_t)max_n + 2 + 31) / 32 * 32; }
 
+// Dynamic shared memory of the large-graph sampler: the preorder chunk.
+constexpr size_t large_smem_bytes(int bt) { return (size_t)kPreChunkPerThread * bt * sizeof(unsigned long long); }
+
 // Graphs of at most kSmemMaxN vertices run the shared-memory kernel at any
 // shape; up to kTierMaxVertices the same kernel with its last words in the
 // workspace tail; larger graphs the large-graph kernel, built for 256
-// threads and more, with no dynamic shared memory (the SM's on-chip memory
-// goes to L1).
+// threads and more, whose only shared array is the preorder chunk (the rest
+// of the SM's on-chip memory goes to L1).
 template <int BT>
 cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
 {
@@ -1696,7 +1727,11 @@ cudaError_t launch_sampler(int grid, cudaStream_t st, const SampleParams &p)
         sample_aggregate_smem_kernel<BT, true><<<grid, BT, bytes, st>>>(p);
     } else {
         if constexpr (BT >= 256) {
-            sample_aggregate_large_kernel<BT><<<grid, BT, 0, st>>>(p);
+            constexpr size_t bytes = large_smem_bytes(BT);
+            cudaError_t e = cudaFuncSetAttribute(sample_aggregate_large_kernel<BT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            if (e != cudaSuccess) return e;
+            sample_aggregate_large_kernel<BT><<<grid, BT, bytes, st>>>(p);
         } else {
             return cudaErrorInvalidConfiguration;
         }
@@ -1740,7 +1775,11 @@ int resident_ctas(int max_n)
             return 0;
     } else {
         if constexpr (BT >= 256) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_large_kernel<BT>, BT, 0) !=
+            constexpr size_t bytes = large_smem_bytes(BT);
+            if (cudaFuncSetAttribute(sample_aggregate_large_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes) != cudaSuccess)
+                return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sample_aggregate_large_kernel<BT>, BT, bytes) !=
                 cudaSuccess)
                 return 0;
         }
@@ -1979,6 +2018,7 @@ int upload_single_desc(Ctx *c)
         gd.rp = c->d_srp;
         gd.ci = c->d_sci;
         gd.path = c->d_spath;
+        gd.pathptr = c->d_spathptr;
         gd.orig = c->d_orig;
         gd.rp_in = c->d_rp;
     }
