@@ -132,7 +132,7 @@ int tune_single(Ctx *c, int *bt, int *cps)
     key.pivot_deg_log2 = ilog2_ceil(std::max(1, rp2[1] - rp2[0]));
     key.graphs_log2 = 0;
     key.sms = c->num_sms;
-    int rc = ust::upload_single_desc(c);
+    int rc = ust::upload_single_desc(c, true);
     if (rc) return rc;
     const long long max_rounds =
         c->max_pop_rounds > 0 ? c->max_pop_rounds

@@ -49,6 +49,7 @@ GraphDesc desc_of(const Ctx *c, int g, long long tree_begin)
     d.aoff = c->baoff[g];
     d.orig = nullptr;
     d.rp_in = nullptr;
+    d.ncore = d.n;
     return d;
 }
 

@@ -32,6 +32,13 @@ enum : int {
 // launch reads one per work item.
 struct GraphDesc {
     int n, u;
+    // The large-graph sampler builds trees on sampler ids below ncore only
+    // (n: all of them). The ids from ncore on are pendant vertices (degree
+    // 1, not the pivot): every spanning tree hangs each from its one
+    // neighbour, a draw of one by a core vertex closes a 2-cycle that is
+    // popped at once (the core vertex takes its next stack entry), and its
+    // counts follow from its neighbour's after the launch.
+    int ncore;
     uint32_t graph;            // fourth Philox counter word
     long long voff;            // offset of the graph's vertices in batch-wide arrays
     long long tree_begin;      // first tree id of the graph in this launch
@@ -162,6 +169,8 @@ struct Ctx {
     int32_t *d_spathptr = nullptr;                  // where sampler vertex v's path starts in d_spath
     int64_t spath_cap = 0;
     int spivot = 0;                                 // the pivot's sampler id
+    int relabel_core = 0;  // sampler ids below: core vertices; from here on: pendant ones
+    int ncore = 0;         // the current pivot's core (n when the pivot itself is pendant)
 
     // sampling
     LaunchCfg cfg;                  // single graph: the sampler's launch shape
@@ -289,8 +298,10 @@ int alloc_batch_sampler(Ctx *c, int block_threads, int ctas_per_sm);
 int tune_launch(Ctx *c, const TuneKey &key, const GraphDesc *d_graphs, const long long *d_items, int ngraphs,
                 long long items, int max_n, long long max_rounds, int64_t *d_scratch, LaunchCfg *out,
                 double *best_ms_per_item);
-// Uploads the single graph's sampler descriptor and item starts when they changed.
-int upload_single_desc(Ctx *c);
+// Uploads the single graph's sampler descriptor and item starts when they
+// changed; prune: trees on the core of a relabelled graph only (count
+// aggregation without arc counts).
+int upload_single_desc(Ctx *c, bool prune);
 // mode 0: aggregate trees [t0, t1) into d_out (int64 n) - added, not assigned.
 // mode 1: export next/pops of trees [t0, t1) to device buffers.
 int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, int32_t *d_next_out,

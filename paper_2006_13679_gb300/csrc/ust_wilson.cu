@@ -250,15 +250,26 @@ constexpr int kPreorderSpin = 512;
 // Input id of sampler vertex v (identity when the graph is not relabelled).
 __device__ __forceinline__ int orig_of(const GraphDesc &g, int v) { return g.orig ? __ldg(g.orig + v) : v; }
 
-// Stack entry k of sampler vertex x whose input id is o: the row is x's,
-// the Philox counter o's.
-__device__ __forceinline__ int stack_entry_of(const GraphDesc &g, uint32_t key0, uint32_t key1, int x, int o,
-                                              uint32_t k, uint32_t tree)
+// Stack entry k of sampler vertex x whose input id is o (the row is x's, the
+// Philox counter o's), skipping the entries that name pendant vertices (ids
+// from ncore on): such an entry and the pendant vertex, whose every entry
+// names x, form a 2-cycle, popped at once. Returns the entry taken and its
+// depth. At most 64 deg(x) + 1024 entries are skipped; the caller's range
+// check reports an id still at or above ncore. Not inlined: the kernel calls
+// it only for the draws that need it, and its loop stays out of the hot path's
+// registers.
+__device__ __noinline__ int2 core_entry_of(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                           uint32_t graph, uint32_t key0, uint32_t key1, int x, int o, uint32_t k,
+                                           uint32_t tree, int ncore)
 {
-    const int b = __ldg(g.rp + x);
-    const int e = __ldg(g.rp + x + 1);
-    const unsigned long long r = philox_x64((uint32_t)o, k, tree, g.graph, key0, key1);
-    return __ldg(g.ci + b + (int)__umul64hi(r, (unsigned long long)(e - b)));
+    const int b = __ldg(rp + x), deg = __ldg(rp + x + 1) - b;
+    const uint32_t lim = k + 64u * (uint32_t)deg + 1024u;
+    for (;;) {
+        const unsigned long long r = philox_x64((uint32_t)o, k, tree, graph, key0, key1);
+        const int y = __ldg(ci + b + (int)__umul64hi(r, (unsigned long long)deg));
+        if (y < ncore || k >= lim) return make_int2(y, (int)k);
+        ++k;
+    }
 }
 
 // Appends val for the lanes with flag set, at most cap entries in all (later
@@ -356,6 +367,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
     } while (0)
 
     unsigned long long my_draws = 0, my_rounds = 0;
+    unsigned long long my_skips = 0;  // stack entries skipped over pendant vertices (every thread)
     int my_max_rounds = 0, my_max_pops = 0;
 
     for (;;) {
@@ -364,7 +376,9 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         GraphDesc gd;
         long long t;
         if (!item_graph(p, s_tree, gd, t)) break;
-        const int n = gd.n, u = gd.u;
+        // the tree is built on the core, ids below ncore (pendant vertices
+        // above are never drawn into it)
+        const int n = gd.ncore, u = gd.u;
         const uint32_t tree = (uint32_t)t;
         const LargeWords W{CWg, reinterpret_cast<uint32_t *>(ordp)};
         if (tid == 0) {
@@ -398,8 +412,15 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 if (v < n) {
+                    int dep = 0;
+                    if (y[k] >= n) {  // a pendant vertex: its 2-cycle pops at once
+                        const int2 e = core_entry_of(gd.rp, gd.ci, gd.graph, p.key0, p.key1, v, o[k], 0u, tree, n);
+                        y[k] = e.x;
+                        dep = e.y;
+                        my_skips += (unsigned)dep;
+                    }
                     NXT[v] = y[k];
-                    DEP[v] = 0;
+                    DEP[v] = dep;
                     if (y[k] >= 0 && y[k] != u) atomicAdd(W.w(checked_vertex(y[k], n, u, 1, p)), kChild);  // u's counters are never needed
                 }
             }
@@ -510,9 +531,11 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
                 if (x == u) continue;
                 const uint32_t k = (uint32_t)DEP[x] + 1u;
                 const int old = checked_vertex(NXT[x], n, u, 5, p);
-                const int y = checked_vertex(stack_entry_of(gd, p.key0, p.key1, x, orig_of(gd, x), k, tree), n, u, 5, p);
+                const int2 e = core_entry_of(gd.rp, gd.ci, gd.graph, p.key0, p.key1, x, orig_of(gd, x), k, tree, n);
+                const int y = checked_vertex(e.x, n, u, 5, p);
+                my_skips += (uint32_t)e.y - k;
                 NXT[x] = y;
-                DEP[x] = (int)k;
+                DEP[x] = e.y;
                 *W.mark(x) = (uint32_t)rounds;
                 pos[x] = i;
                 if (old != u) atomicAdd(W.hi(old), 0xFFFFFFFFu);  // one child less
@@ -1014,6 +1037,9 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_large
         atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
         for (int k = 0; k < 8; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
     }
+    // a skipped entry is one pop of the core vertex and one of the pendant
+    // vertex it named (whose first draws the host adds)
+    if (my_skips) atomicAdd(p.stats + 0, 2ull * my_skips);
 }
 // ---------------------------------------------------------------------------
 // The same three phases for graphs of at most kTierMaxVertices vertices
@@ -1684,12 +1710,19 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 
 // out[v] += sum over partial rows of Rp[c][v] (exact, fixed order).
 // Row v of Rp belongs to input vertex orig[v] (v itself when orig is NULL).
+// out[orig(v)] += the launch's count of v, summed over the CTAs' rows. A
+// pendant vertex v (id ncore and up) lies below its one neighbour w in every
+// tree, and its BFS path is w's with the edge (w, v) in front, which every
+// tree uses downwards: its count per tree is 1 + w's.
 __global__ void reduce_counts_kernel(int n, int rows, const int32_t *__restrict__ Rp, long long *__restrict__ out,
-                                     const int32_t *__restrict__ orig)
+                                     const int32_t *__restrict__ orig, int ncore, long long trees,
+                                     const int32_t *__restrict__ srp, const int32_t *__restrict__ sci)
 {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        long long s = 0;
-        for (int c = 0; c < rows; ++c) s += Rp[(long long)c * n + v];
+        const bool pendant = v >= ncore;
+        const int src = pendant ? sci[srp[v]] : v;
+        long long s = pendant ? trees : 0;
+        for (int c = 0; c < rows; ++c) s += Rp[(long long)c * n + src];
         out[orig ? orig[v] : v] += s;
     }
 }
@@ -1991,7 +2024,7 @@ int tune_launch(Ctx *c, const TuneKey &key, const GraphDesc *d_graphs, const lon
 
 // The single graph's descriptor: uploaded when B_u (pivot, path space) or
 // the rows changed.
-int upload_single_desc(Ctx *c)
+int upload_single_desc(Ctx *c, bool prune)
 {
     GraphDesc gd{};
     gd.n = c->n;
@@ -2010,6 +2043,7 @@ int upload_single_desc(Ctx *c)
     gd.aoff = 0;
     gd.orig = nullptr;
     gd.rp_in = nullptr;
+    gd.ncore = c->n;
     // the large-graph sampler's relabelled view (not with the walk rows of
     // the biconnected-component variant, which the context swaps in)
     const bool relabelled = c->relabel && !c->blocks;
@@ -2021,11 +2055,13 @@ int upload_single_desc(Ctx *c)
         gd.pathptr = c->d_spathptr;
         gd.orig = c->d_orig;
         gd.rp_in = c->d_rp;
+        if (prune) gd.ncore = c->ncore;
     }
     const GraphDesc &o = c->single_desc;
     const bool same = o.n == gd.n && o.u == gd.u && o.graph == gd.graph && o.rp == gd.rp && o.ci == gd.ci &&
                       o.bpar == gd.bpar && o.path == gd.path && o.pathptr == gd.pathptr && o.pchild == gd.pchild &&
-                      o.powner == gd.powner && o.fc == gd.fc && o.orig == gd.orig && o.rp_in == gd.rp_in;
+                      o.powner == gd.powner && o.fc == gd.fc && o.orig == gd.orig && o.rp_in == gd.rp_in &&
+                      o.ncore == gd.ncore;
     if (!c->single_desc_valid || !same) {
         c->single_desc = gd;
         const long long starts[2] = {0, kOpenEnd};
@@ -2048,9 +2084,13 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         UST_CUDA_TRY(cudaMemsetAsync(c->d_Rp, 0, (size_t)grid * c->n * sizeof(int32_t), c->stream));
     UST_CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, 32 * sizeof(int64_t), c->stream));
 
-    const int drc = upload_single_desc(c);
+    // pendant vertices are left out of the trees only when counts are
+    // aggregated without arc counts (sampled trees and arcs need them all)
+    const bool prune = mode == 0 && !c->d_ecount_tmp;
+    const int drc = upload_single_desc(c, prune);
     if (drc) return drc;
     const bool relabelled = c->relabel && !c->blocks;
+    const int ncore = (relabelled && prune) ? c->ncore : c->n;
     SampleParams p{};
     p.max_n = c->n;
     p.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
@@ -2093,7 +2133,8 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         const int blocks = (int)std::min<int64_t>((c->n + threads - 1) / threads, (int64_t)c->num_sms * 8);
         reduce_counts_kernel<<<blocks, threads, 0, c->stream>>>(c->n, grid, c->d_Rp,
                                                                  reinterpret_cast<long long *>(d_out),
-                                                                 relabelled ? c->d_orig : nullptr);
+                                                                 relabelled ? c->d_orig : nullptr, ncore, t1 - t0,
+                                                                 c->d_srp, c->d_sci);
         phase_end(c, Ctx::kEvReduce);
         c->launches += 1;
         UST_CUDA_TRY(cudaGetLastError());
@@ -2105,6 +2146,8 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
     if (status & kStatusJumpSteps) return fail(c, UST_ETIMEOUT, "pointer jumping did not converge");
     if (status)
         return fail(c, UST_ECUDA, "sampler reported an inconsistent state (check " + std::to_string(c->h_stats[6]) + ")");
+    // the first draws of the pendant vertices left out of the trees
+    c->h_stats[0] += (t1 - t0) * (int64_t)(c->n - ncore);
     c->last_trees = t1 - t0;
     c->last_draws = c->h_stats[0];
     for (int k = 0; k < 12; ++k) c->last_phase_cycles[k] = c->h_stats[8 + k];
@@ -2275,6 +2318,7 @@ __global__ void __launch_bounds__(kPrepThreads) noalloc_prepare_kernel(int n, in
         d.aoff = 0;
         d.orig = nullptr;
         d.rp_in = nullptr;
+        d.ncore = n;
         *desc = d;
         item_start[0] = 0;
         item_start[1] = kOpenEnd;
@@ -2362,7 +2406,7 @@ extern "C" int ust_tree_counts_noalloc(const int32_t *row_ptr, const int32_t *co
         const int grid = (int)std::min<int64_t>(kNoAllocCtas, t1 - t0);
         if (launch_sampler<kNoAllocThreads>(grid, st, p) != cudaSuccess) return UST_ECUDA;
         reduce_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, grid, Rp, reinterpret_cast<long long *>(R_out),
-                                                                nullptr);
+                                                                nullptr, n, 0, nullptr, nullptr);
         if (cudaGetLastError() != cudaSuccess) return UST_ECUDA;
         if (cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return UST_ECUDA;

@@ -507,3 +507,56 @@ def test_block_variant_rejected_for_batches(pkg):
     with pytest.raises(pkg.UstError) as ei:
         pkg.USTBatch([(g.row_ptr, g.col_idx) for g in gs], [0, 0], wilson_blocks=True)
     assert ei.value.code == pkg.UST_EINVAL
+
+
+def _with_pendants(g, u, k, seed):
+    """g plus k new vertices of degree 1, each joined to a random vertex of g
+    (the first three to the pivot u), and a path of two new vertices hanging
+    from vertex 0: the vertex at its end is pendant, its neighbour is not."""
+    rng = np.random.default_rng(seed)
+    deg = np.diff(g.row_ptr)
+    src = [np.repeat(np.arange(g.n), deg), np.arange(g.n, g.n + k), [g.n + k, g.n + k + 1]]
+    tgt = rng.integers(0, g.n, k)
+    tgt[:3] = u
+    dst = [g.col_idx, tgt, [0, g.n + k]]
+    return synth.from_edges(g.n + k + 2, np.concatenate(src), np.concatenate(dst), lcc=False)
+
+
+def test_pendant_vertices_left_out_of_the_trees(pkg, orc):
+    """Above 65,535 vertices the sampler builds its trees on the vertices of
+    degree 2 and more (and the pivot) and derives the counts of degree-1
+    vertices from their neighbours': R and the draw count bit-exact with the
+    oracle's Wilson on the whole graph, here with a quarter of the vertices
+    pendant, three of them at the pivot; sampled trees (every vertex) too."""
+    base = synth.rmat(17, 8, seed=2)
+    u = synth.max_degree_vertex(base)
+    g = _with_pendants(base, u, 40000, seed=3)
+    assert g.n > 0xFFFF and (np.diff(g.row_ptr) == 1).sum() > 40000
+    _, _, par = orc.bfs(g, u)
+    with make(pkg, g, u) as h:
+        h.sample_aggregate(300, 17)
+        R_ref, steps = orc.sample_aggregate(g, u, par, 0, 300, 17, threads=THREADS)
+        assert np.array_equal(h.counts(), R_ref)
+        assert h.info()["draws"] == steps
+        nxt, pops = h.sample_trees(7, 2, 17, with_pops=True)
+        for i in range(2):
+            ref, ref_pops, _ = orc.wilson(g, u, 7 + i, 17)
+            assert np.array_equal(nxt[i], ref) and np.array_equal(pops[i], ref_pops)
+
+
+def test_pendant_pivot_keeps_every_vertex(pkg, orc):
+    """After ust_reset to a pivot of degree 1 the trees take every vertex (the
+    pivot is no pendant vertex of its own trees); back at a hub the pendant
+    vertices are left out again. R bit-exact both times."""
+    base = synth.rmat(17, 8, seed=2)
+    u = synth.max_degree_vertex(base)
+    g = _with_pendants(base, u, 20000, seed=5)
+    leaf = g.n - 1  # the end of the hanging path
+    with make(pkg, g, u) as h:
+        for pivot in (leaf, u):
+            h.reset(pivot)
+            h.sample_aggregate(200, 29)
+            _, _, par = orc.bfs(g, pivot)
+            R_ref, steps = orc.sample_aggregate(g, pivot, par, 0, 200, 29, threads=THREADS)
+            assert np.array_equal(h.counts(), R_ref), pivot
+            assert h.info()["draws"] == steps
