@@ -40,7 +40,11 @@ SEED = 0
 # vertex-tree of the captured launch, the workloads it is scaled to, and the sha1 of
 # the sampler's sources (the kernel and the relabelling that orders its memory) when
 # it was taken.
-TRAFFIC_CAPTURES = []
+TRAFFIC_CAPTURES = [
+    # R-MAT scale 22, one launch of 1,520 trees: 894.5 GB read + 345.7 GB written
+    {"applies_to": ["rmat22"], "sha1": "8d0bcbe35fd95050f52450c95178487ecbece2bd",
+     "bytes_per_vertex_tree": 1240.14e9 / (1520 * 2394915)},
+]
 SAMPLER_SOURCES = ("ust_wilson.cu", "ust_relabel.cu")
 
 # workload -> (description, oracle sample in trees for the CPU baseline; None = all)
