@@ -109,8 +109,8 @@ typedef struct {
                                with B_u (ust_init, ust_reset); arc counts stay per input arc.
                                Single-graph contexts only (ust_init_batch: UST_EINVAL)
                                [0 = plain Wilson rooted at u] */
-    int32_t autotune;       /* launch shapes of the sampler: 1 = tuned, -1 = fixed table, 0 = default
-                               [tuned for ust_init_batch, fixed table for ust_init]. Tuning times every
+    int32_t autotune;       /* launch shapes of the sampler: 1 = tuned, -1 or 0 = fixed table
+                               [0]. Tuning times every
                                candidate shape (threads per CTA x CTAs per SM that fit) on a probe of
                                the launch's own work at context creation and keeps the fastest; the
                                choice is remembered for the process per workload key (kernel, size

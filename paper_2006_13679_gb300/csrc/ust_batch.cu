@@ -83,7 +83,7 @@ int batch_prepare(Ctx *c, bool fill)
     UST_CUDA_TRY(cudaMemcpyAsync(c->h_prep_out, c->d_prep_out, (size_t)B * 3 * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, c->stream));
     phase_end(c, Ctx::kEvBfs);
-    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    UST_SYNC_TRY(fill ? "batch B_u with paths" : "batch B_u");
     for (int g = 0; g < B; ++g) {
         const int st = c->h_prep_out[g];
         if (st & 1) return fail(c, UST_ENOTCONNECTED, "graph " + std::to_string(g) + " is not connected");
@@ -361,7 +361,7 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
     c->ecc = *std::max_element(c->becc.begin(), c->becc.end());
     c->farness = c->bpoff[B];
 
-    if (op.autotune >= 0 && op.block_threads == 0 && op.ctas_per_sm == 0) {
+    if (op.autotune > 0 && op.block_threads == 0 && op.ctas_per_sm == 0) {
         rc = tune_batch_classes(c, hrp);
         if (rc) return rc;
     }
@@ -392,7 +392,7 @@ int batch_init(Ctx *c, const ust_csr *gs, const int32_t *pivots, int32_t count, 
         return fail(c, UST_ENOMEM, "solve results");
     if (cudaMallocHost(&c->h_results, (size_t)B * sizeof(SolveResult)) != cudaSuccess)
         return fail(c, UST_ENOMEM, "pinned solve results");
-    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    UST_SYNC_TRY("batch set-up");
     return UST_OK;
 }
 

@@ -18,6 +18,13 @@
         }                                                                           \
     } while (0)
 
+// Waits for the context's stream; an error names the step that waited.
+#define UST_SYNC_TRY(what)                                                                   \
+    do {                                                                                     \
+        cudaError_t _e = cudaStreamSynchronize(c->stream);                                   \
+        if (_e != cudaSuccess) return ust::fail(c, UST_ECUDA, std::string(what) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
 namespace ust {
 
 // Device status word bits (written by kernels, read by the host).

@@ -233,10 +233,10 @@ struct LargeWords {
 };
 
 // Preorder phase: vertices per chunk and thread (a packed word each in
-// shared memory, 64 KB at 1,024 threads), the tag and link values of the
+// shared memory, 32 KB at 1,024 threads), the tag and link values of the
 // high words, and the rounds a warp waits for the parents of deferred
 // vertices before leaving them to the next pass.
-constexpr int kPreChunkPerThread = 8;
+constexpr int kPreChunkPerThread = 4;
 constexpr int kPreBatch = 4;  // of them loaded together
 // Marks a leaf's entry in the arrival log (its offset field; offsets < 2^31).
 constexpr int32_t kLeafBit = (int32_t)0x80000000u;
@@ -1227,7 +1227,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                     const int v = cand;
                     cand += BT;
                     if (v != u && lo16[v] == kFinal16) {
-                        y[k] = nx16[v];
+                        y[k] = checked_vertex(nx16[v], n, u, 25, p);
                         if (y[k] != u) break;
                     }
                 }
@@ -1237,14 +1237,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     if (y[k] != u && half_add(lo32, y[k], -1) == 1u) {
-                        y[k] = nx16[y[k]];  // y peeled: remove its out-edge next
+                        y[k] = checked_vertex(nx16[y[k]], n, u, 25, p);  // y peeled: remove its out-edge next
                     } else {
                         y[k] = u;
                         while (cand < n) {
                             const int v = cand;
                             cand += BT;
                             if (v != u && lo16[v] == kFinal16) {
-                                y[k] = nx16[v];
+                                y[k] = checked_vertex(nx16[v], n, u, 25, p);
                                 if (y[k] != u) break;
                             }
                         }
@@ -1290,9 +1290,10 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             }
             // (a) pop: every vertex on a cycle advances to its next stack entry
             for (int i = tid; i < nX; i += BT) {
-                const int x = X[i];
+                const int x = checked_vertex(X[i], n, u, 20, p);
+                if (x == u) continue;
                 const int k = pop[x] + 1;
-                const int y = stack_entry(gd, p.key0, p.key1, x, (uint32_t)k, tree);
+                const int y = checked_vertex(stack_entry(gd, p.key0, p.key1, x, (uint32_t)k, tree), n, u, 21, p);
                 pop[x] = k;
                 nxt[x] = y;
                 nx16[x] = (uint16_t)y;
@@ -1321,7 +1322,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             //     walk are not marked: short walks skip the bookkeeping.
             const bool mark_on = s_mark_on;
             for (int i = tid; i < nX; i += BT) {
-                int y = nx16[X[i]];
+                int y = checked_vertex(nx16[checked_vertex(X[i], n, u, 22, p)], n, u, 22, p);
                 int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = lo16[y];
@@ -1339,7 +1340,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                         lo16[y] = (uint16_t)vis;
                     }
                     ++len;
-                    y = nx16[y];
+                    y = checked_vertex(nx16[y], n, u, 23, p);
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
@@ -1367,18 +1368,18 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             //     keep their stack tops.
             for (int i = tid; i < nX; i += BT) {
                 const int kind = classify_node(Sx, i, nX);
-                int y = X[i];
+                int y = checked_vertex(X[i], n, u, 24, p);
                 if (kind == 1) {
                     const int len = wlen[i];
                     lo16[y] = kFinal16;
                     for (int k = 0; k < len; ++k) {
-                        y = nx16[y];
+                        y = checked_vertex(nx16[y], n, u, 24, p);
                         lo16[y] = kFinal16;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
                         Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
-                        y = nx16[y];
+                        y = checked_vertex(nx16[y], n, u, 24, p);
                         if (lo16[y] == stamp) break;
                     }
                     if (lo16[y] != stamp) s_err = 1;  // a cycle segment ends at a redrawn vertex
@@ -1451,7 +1452,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                 cand += BT;
                 if (v != u && C[v] == 0u) {
                     sv = v;
-                    spar = nxt[v];
+                    spar = checked_vertex(nxt[v], n, u, 26, p);
                     break;
                 }
             }
@@ -1469,7 +1470,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                     cand += BT;
                     if (v != u && C[v] == 0u) {
                         sv = v;
-                        spar = nxt[v];
+                        spar = checked_vertex(nxt[v], n, u, 26, p);
                         break;
                     }
                 }
@@ -1480,7 +1481,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     old[k] = (par[k] >= 0) ? atomicAdd(&C[par[k]], carry[k] - kC16) : 0u;
-                    gp[k] = (par[k] >= 0 && par[k] != u) ? nxt[par[k]] : -1;
+                    gp[k] = (par[k] >= 0 && par[k] != u) ? checked_vertex(nxt[par[k]], n, u, 26, p) : -1;
                 }
                 bool any = false;
 #pragma unroll
@@ -1502,7 +1503,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                                 cand += BT;
                                 if (v != u && C[v] == 0u) {
                                     sv = v;
-                                    spar = nxt[v];
+                                    spar = checked_vertex(nxt[v], n, u, 26, p);
                                     break;
                                 }
                             }
@@ -1524,7 +1525,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 const bool ok = v < n && v != u;
-                pa[k] = ok ? nxt[v] : u;
+                pa[k] = ok ? checked_vertex(nxt[v], n, u, 27, p) : u;
                 of[k] = ok ? off[v] : 0;
             }
 #pragma unroll
@@ -1974,7 +1975,7 @@ int probe_launch(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, const 
     c->launches += 1;
     if (e != cudaSuccess) return fail(c, UST_ECUDA, std::string("tuning probe launch: ") + cudaGetErrorString(e));
     UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 32 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    UST_SYNC_TRY("tuning probe (" + std::to_string(cfg.bt) + " threads, " + std::to_string(grid) + " CTAs)");
     if (c->h_stats[5] & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
     if (c->h_stats[5])
         return fail(c, UST_ECUDA, "sampler reported an inconsistent state (check " + std::to_string(c->h_stats[6]) + ")");
@@ -2140,7 +2141,7 @@ int run_sampler(Ctx *c, int64_t t0, int64_t t1, uint64_t seed, int64_t *d_out, i
         UST_CUDA_TRY(cudaGetLastError());
     }
     UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 32 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    UST_SYNC_TRY("sampler");
     const int status = (int)c->h_stats[5];
     if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
     if (status & kStatusJumpSteps) return fail(c, UST_ETIMEOUT, "pointer jumping did not converge");
@@ -2525,7 +2526,7 @@ int run_batch_sampler(Ctx *c, const LaunchCfg &cfg, const GraphDesc *d_graphs, c
     c->launches += 1;
     if (e != cudaSuccess) return fail(c, UST_ECUDA, std::string("batch sampler launch: ") + cudaGetErrorString(e));
     UST_CUDA_TRY(cudaMemcpyAsync(c->h_stats, c->d_stats, 32 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    UST_SYNC_TRY("batch sampler (" + std::to_string(cfg.bt) + " threads, " + std::to_string(grid) + " CTAs)");
     const int status = (int)c->h_stats[5];
     if (status & kStatusPopRounds) return fail(c, UST_ETIMEOUT, "a tree exceeded max_pop_rounds");
     if (status & kStatusJumpSteps) return fail(c, UST_ETIMEOUT, "pointer jumping did not converge");
