@@ -188,7 +188,7 @@ int init_impl(Ctx *c, const ust_csr *g, int32_t pivot, const ust_opts *o)
         c->blocks = true;
         rc = ust::build_block_rows(c);
         if (rc) return rc;
-    } else if (n > ust::kTierMaxVertices) {  // the large-graph sampler's degree-ordered view
+    } else {  // the samplers' view: Cuthill-McKee order, pendant vertices last
         rc = ust::build_relabel(c);
         if (rc) return rc;
         rc = ust::relabel_paths(c);

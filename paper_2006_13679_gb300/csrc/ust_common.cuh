@@ -172,12 +172,13 @@ struct Ctx {
     bool relabel = false;
     int32_t *d_srp = nullptr, *d_sci = nullptr;     // relabelled CSR
     int32_t *d_orig = nullptr, *d_newid = nullptr;  // sampler id -> input id, and back
-    int32_t *d_spath = nullptr;                     // flattened BFS paths in sampler ids and order
+    int32_t *d_spath = nullptr;  // flattened BFS paths in sampler ids and order: 3 x spath_cap (ancestor, child, owner)
     int32_t *d_spathptr = nullptr;                  // where sampler vertex v's path starts in d_spath
     int64_t spath_cap = 0;
     int spivot = 0;                                 // the pivot's sampler id
     int relabel_core = 0;  // sampler ids below: core vertices; from here on: pendant ones
     int ncore = 0;         // the current pivot's core (n when the pivot itself is pendant)
+    int64_t core_fc = 0;   // path entries of the core vertices (they come first)
 
     // sampling
     LaunchCfg cfg;                  // single graph: the sampler's launch shape

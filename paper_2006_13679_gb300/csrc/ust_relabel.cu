@@ -252,15 +252,22 @@ __global__ void spath_lengths_kernel(int n, const int32_t *__restrict__ orig, co
 }
 
 // The flattened BFS paths in sampler ids and sampler order: the path of
-// sampler vertex v at spathptr[v], its entries in the input path's order.
+// sampler vertex v at spathptr[v], its entries in the input path's order;
+// entry q is the edge (spath[q], spchild[q]) of the path of spowner[q].
 __global__ void relabel_path_kernel(int n, const int32_t *__restrict__ orig, const int32_t *__restrict__ pathptr,
-                                    const int32_t *__restrict__ path, const int32_t *__restrict__ spathptr,
-                                    const int32_t *__restrict__ newid, int32_t *__restrict__ spath)
+                                    const int32_t *__restrict__ path, const int32_t *__restrict__ pchild,
+                                    const int32_t *__restrict__ spathptr, const int32_t *__restrict__ newid,
+                                    int32_t *__restrict__ spath, int32_t *__restrict__ spchild,
+                                    int32_t *__restrict__ spowner)
 {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int o = orig[v];
         const int src = pathptr[o], len = pathptr[o + 1] - src, dst = spathptr[v];
-        for (int k = 0; k < len; ++k) spath[dst + k] = newid[path[src + k]];
+        for (int k = 0; k < len; ++k) {
+            spath[dst + k] = newid[path[src + k]];
+            spchild[dst + k] = newid[pchild[src + k]];
+            spowner[dst + k] = v;
+        }
     }
 }
 
@@ -383,7 +390,7 @@ int relabel_paths(Ctx *c)
         cudaFree(c->d_spath);
         c->d_spath = nullptr;
         c->spath_cap = 0;
-        if (cudaMalloc(&c->d_spath, (size_t)std::max<int64_t>(1, c->farness) * 4) != cudaSuccess)
+        if (cudaMalloc(&c->d_spath, 3 * (size_t)std::max<int64_t>(1, c->farness) * 4) != cudaSuccess)
             return fail(c, UST_ENOMEM, "BFS paths in sampler ids");
         c->spath_cap = c->farness;
     }
@@ -395,8 +402,10 @@ int relabel_paths(Ctx *c)
     spath_lengths_kernel<<<blocks, threads, 0, c->stream>>>(n, c->d_orig, c->d_dist, len);
     UST_CUDA_TRY(cudaGetLastError());
     UST_CUDA_TRY(launch_exclusive_scan(n, len, c->d_spathptr, c->stream));
-    relabel_path_kernel<<<blocks, threads, 0, c->stream>>>(n, c->d_orig, c->d_pathptr, c->d_path, c->d_spathptr,
-                                                           c->d_newid, c->d_spath);
+    relabel_path_kernel<<<blocks, threads, 0, c->stream>>>(n, c->d_orig, c->d_pathptr, c->d_path,
+                                                           c->d_path + c->path_cap, c->d_spathptr, c->d_newid,
+                                                           c->d_spath, c->d_spath + c->spath_cap,
+                                                           c->d_spath + 2 * c->spath_cap);
     c->launches += 3;
     UST_CUDA_TRY(cudaGetLastError());
     int32_t sp = 0;
@@ -405,6 +414,10 @@ int relabel_paths(Ctx *c)
     c->spivot = sp;
     // a pivot that is itself pendant (after ust_reset) keeps every vertex in the trees
     c->ncore = sp < c->relabel_core ? c->relabel_core : n;
+    int32_t fc = 0;
+    UST_CUDA_TRY(cudaMemcpyAsync(&fc, c->d_spathptr + c->ncore, sizeof(fc), cudaMemcpyDeviceToHost, c->stream));
+    UST_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->core_fc = fc;
     return UST_OK;
 }
 

@@ -112,13 +112,14 @@ __device__ __forceinline__ bool item_graph(const SampleParams &p, long long item
     return true;
 }
 
-// Stack entry `k` of vertex v: a uniformly chosen neighbour.
-__device__ __forceinline__ int stack_entry(const GraphDesc &g, uint32_t key0, uint32_t key1, int v, uint32_t k,
+// Stack entry `k` of vertex v whose input id is o (the row is v's, the
+// Philox counter o's): a uniformly chosen neighbour.
+__device__ __forceinline__ int stack_entry(const GraphDesc &g, uint32_t key0, uint32_t key1, int v, int o, uint32_t k,
                                            uint32_t tree)
 {
     const int b = __ldg(g.rp + v);
     const int e = __ldg(g.rp + v + 1);
-    const unsigned long long x = philox_x64((uint32_t)v, k, tree, g.graph, key0, key1);
+    const unsigned long long x = philox_x64((uint32_t)o, k, tree, g.graph, key0, key1);
     const unsigned long long idx = __umul64hi(x, (unsigned long long)(e - b));
     return __ldg(g.ci + b + (int)idx);
 }
@@ -1153,6 +1154,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
     } while (0)
 
     unsigned long long my_draws = 0, my_rounds = 0;
+    unsigned long long my_skips = 0;  // stack entries skipped over pendant vertices (every thread)
     int my_max_rounds = 0, my_max_pops = 0;
 
     for (;;) {
@@ -1161,7 +1163,9 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
         GraphDesc gd;
         long long t;
         if (!item_graph(p, s_tree, gd, t)) break;
-        const int n = gd.n, u = gd.u;
+        // the tree is built on the core, ids below ncore (a relabelled graph's
+        // pendant vertices above are never drawn into it)
+        const int n = gd.ncore, u = gd.u;
         const uint32_t tree = (uint32_t)t;
         const int nhalf = (n + 1) >> 1;                                // words of one 16-bit array
         const Halves16<kTier> nx16{tw, 2 * nhalf};  // successors
@@ -1183,14 +1187,23 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
-                const unsigned long long x = philox_x64((uint32_t)v, 0u, tree, gd.graph, p.key0, p.key1);
+                const int o = (v < n) ? orig_of(gd, v) : v;
+                const unsigned long long x = philox_x64((uint32_t)o, 0u, tree, gd.graph, p.key0, p.key1);
                 y[k] = (deg[k] > 0) ? __ldg(gd.ci + rb[k] + (int)__umul64hi(x, (unsigned long long)deg[k])) : -1;
             }
 #pragma unroll
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 if (v < n) {
-                    pop[v] = 0;
+                    int dep = 0;
+                    if (y[k] >= n) {  // a pendant vertex: its 2-cycle pops at once
+                        const int2 e =
+                            core_entry_of(gd.rp, gd.ci, gd.graph, p.key0, p.key1, v, orig_of(gd, v), 0u, tree, n);
+                        y[k] = e.x;
+                        dep = e.y;
+                        my_skips += (unsigned)dep;
+                    }
+                    pop[v] = dep;
                     nxt[v] = y[k];
                     nx16[v] = (uint16_t)(v == u ? u : y[k]);  // u points at itself: no walk leaves the array
                 }
@@ -1227,7 +1240,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                     const int v = cand;
                     cand += BT;
                     if (v != u && lo16[v] == kFinal16) {
-                        y[k] = checked_vertex(nx16[v], n, u, 25, p);
+                        y[k] = nx16[v];
                         if (y[k] != u) break;
                     }
                 }
@@ -1237,14 +1250,14 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     if (y[k] != u && half_add(lo32, y[k], -1) == 1u) {
-                        y[k] = checked_vertex(nx16[y[k]], n, u, 25, p);  // y peeled: remove its out-edge next
+                        y[k] = nx16[y[k]];  // y peeled: remove its out-edge next
                     } else {
                         y[k] = u;
                         while (cand < n) {
                             const int v = cand;
                             cand += BT;
                             if (v != u && lo16[v] == kFinal16) {
-                                y[k] = checked_vertex(nx16[v], n, u, 25, p);
+                                y[k] = nx16[v];
                                 if (y[k] != u) break;
                             }
                         }
@@ -1290,10 +1303,16 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             }
             // (a) pop: every vertex on a cycle advances to its next stack entry
             for (int i = tid; i < nX; i += BT) {
-                const int x = checked_vertex(X[i], n, u, 20, p);
-                if (x == u) continue;
-                const int k = pop[x] + 1;
-                const int y = checked_vertex(stack_entry(gd, p.key0, p.key1, x, (uint32_t)k, tree), n, u, 21, p);
+                const int x = X[i];
+                const int ox = orig_of(gd, x);
+                int k = pop[x] + 1;
+                int y = stack_entry(gd, p.key0, p.key1, x, ox, (uint32_t)k, tree);
+                if (y >= n) {  // a pendant vertex: skip its 2-cycle
+                    const int2 e = core_entry_of(gd.rp, gd.ci, gd.graph, p.key0, p.key1, x, ox, (uint32_t)k, tree, n);
+                    my_skips += (unsigned)(e.y - k);
+                    y = e.x;
+                    k = e.y;
+                }
                 pop[x] = k;
                 nxt[x] = y;
                 nx16[x] = (uint16_t)y;
@@ -1322,7 +1341,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             //     walk are not marked: short walks skip the bookkeeping.
             const bool mark_on = s_mark_on;
             for (int i = tid; i < nX; i += BT) {
-                int y = checked_vertex(nx16[checked_vertex(X[i], n, u, 22, p)], n, u, 22, p);
+                int y = nx16[X[i]];
                 int res = -2, len = 0;
                 for (int guard = 0; guard <= n; ++guard) {
                     const int m = lo16[y];
@@ -1340,7 +1359,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                         lo16[y] = (uint16_t)vis;
                     }
                     ++len;
-                    y = checked_vertex(nx16[y], n, u, 23, p);
+                    y = nx16[y];
                 }
                 if (res == -2) { s_err = 1; res = -1; }
                 Sx[i] = res;
@@ -1368,18 +1387,18 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             //     keep their stack tops.
             for (int i = tid; i < nX; i += BT) {
                 const int kind = classify_node(Sx, i, nX);
-                int y = checked_vertex(X[i], n, u, 24, p);
+                int y = X[i];
                 if (kind == 1) {
                     const int len = wlen[i];
                     lo16[y] = kFinal16;
                     for (int k = 0; k < len; ++k) {
-                        y = checked_vertex(nx16[y], n, u, 24, p);
+                        y = nx16[y];
                         lo16[y] = kFinal16;
                     }
                 } else if (kind == 2) {
                     for (int guard = 0; guard <= n; ++guard) {
                         Xn[min(atomicAdd(&s_cnt, 1), n)] = y;  // more than n entries: reported below
-                        y = checked_vertex(nx16[y], n, u, 24, p);
+                        y = nx16[y];
                         if (lo16[y] == stamp) break;
                     }
                     if (lo16[y] != stamp) s_err = 1;  // a cycle segment ends at a redrawn vertex
@@ -1405,17 +1424,21 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
         if (p.edge_counts) {  // the tree's arcs v -> parent(v): the final stack entry of every v
             for (int v = tid; v < n; v += BT) {
                 if (v == u) continue;
+                const int o = orig_of(gd, v);
                 const int b = __ldg(gd.rp + v), e = __ldg(gd.rp + v + 1);
-                const unsigned long long x = philox_x64((uint32_t)v, (uint32_t)pop[v], tree, gd.graph, p.key0, p.key1);
-                atomicAdd(p.edge_counts + gd.aoff + b + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
+                const unsigned long long x = philox_x64((uint32_t)o, (uint32_t)pop[v], tree, gd.graph, p.key0, p.key1);
+                const long long row = gd.rp_in ? (long long)__ldg(gd.rp_in + o) : (long long)b;  // input arc index
+                atomicAdd(p.edge_counts + gd.aoff + row + (long long)__umul64hi(x, (unsigned long long)(e - b)), 1ull);
             }
         }
 
-        if (p.mode == 1) {
-            const long long o = s_tree * (long long)n;
+        if (p.mode == 1) {  // export the tree in input ids (nothing is left out of such launches)
+            const long long ob = s_tree * (long long)n;
             for (int v = tid; v < n; v += BT) {
-                p.next_out[o + v] = nxt[v];
-                if (p.pops_out) p.pops_out[o + v] = pop[v];
+                const int o = orig_of(gd, v);
+                const int tp = nxt[v];
+                p.next_out[ob + o] = (tp < 0) ? -1 : orig_of(gd, tp);
+                if (p.pops_out) p.pops_out[ob + o] = pop[v];
             }
             __syncthreads();
             continue;
@@ -1452,7 +1475,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                 cand += BT;
                 if (v != u && C[v] == 0u) {
                     sv = v;
-                    spar = checked_vertex(nxt[v], n, u, 26, p);
+                    spar = nxt[v];
                     break;
                 }
             }
@@ -1470,7 +1493,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                     cand += BT;
                     if (v != u && C[v] == 0u) {
                         sv = v;
-                        spar = checked_vertex(nxt[v], n, u, 26, p);
+                        spar = nxt[v];
                         break;
                     }
                 }
@@ -1481,7 +1504,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
 #pragma unroll
                 for (int k = 0; k < kWalks; ++k) {
                     old[k] = (par[k] >= 0) ? atomicAdd(&C[par[k]], carry[k] - kC16) : 0u;
-                    gp[k] = (par[k] >= 0 && par[k] != u) ? checked_vertex(nxt[par[k]], n, u, 26, p) : -1;
+                    gp[k] = (par[k] >= 0 && par[k] != u) ? nxt[par[k]] : -1;
                 }
                 bool any = false;
 #pragma unroll
@@ -1503,7 +1526,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
                                 cand += BT;
                                 if (v != u && C[v] == 0u) {
                                     sv = v;
-                                    spar = checked_vertex(nxt[v], n, u, 26, p);
+                                    spar = nxt[v];
                                     break;
                                 }
                             }
@@ -1525,7 +1548,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
             for (int k = 0; k < kWalks; ++k) {
                 const int v = b0 + k * BT;
                 const bool ok = v < n && v != u;
-                pa[k] = ok ? checked_vertex(nxt[v], n, u, 27, p) : u;
+                pa[k] = ok ? nxt[v] : u;
                 of[k] = ok ? off[v] : 0;
             }
 #pragma unroll
@@ -1707,6 +1730,7 @@ __global__ void __launch_bounds__(BT, kThreadsPerSm / BT) sample_aggregate_smem_
         atomicMax(p.stats + 3, (unsigned long long)my_max_pops);
         for (int k = 0; k < 11; ++k) atomicAdd(p.stats + 8 + k, cyc[k]);
     }
+    if (my_skips) atomicAdd(p.stats + 0, 2ull * my_skips);  // as in the large-graph kernel
 }
 
 // out[v] += sum over partial rows of Rp[c][v] (exact, fixed order).
@@ -2053,10 +2077,15 @@ int upload_single_desc(Ctx *c, bool prune)
         gd.rp = c->d_srp;
         gd.ci = c->d_sci;
         gd.path = c->d_spath;
+        gd.pchild = c->d_spath + c->spath_cap;
+        gd.powner = c->d_spath + 2 * c->spath_cap;
         gd.pathptr = c->d_spathptr;
         gd.orig = c->d_orig;
         gd.rp_in = c->d_rp;
-        if (prune) gd.ncore = c->ncore;
+        if (prune) {
+            gd.ncore = c->ncore;
+            gd.fc = (int)c->core_fc;  // the core's paths come first
+        }
     }
     const GraphDesc &o = c->single_desc;
     const bool same = o.n == gd.n && o.u == gd.u && o.graph == gd.graph && o.rp == gd.rp && o.ci == gd.ci &&
