@@ -38,11 +38,11 @@ METRIC = "USTs sampled+aggregated/sec and diag(L†) wall time on 1 GB300; % of 
 SEED = 0
 # DRAM traffic of the sampler from ncu captures of the sampler kernel: bytes per
 # vertex-tree of the captured launch, the workloads it is scaled to, and the sha1 of
-# the sampler's sources (the kernel and the relabelling that orders its memory) when
-# it was taken.
+# the sampler's code (the kernel and the relabelling that orders its memory, without
+# comments; sampler_sha1) when it was taken.
 TRAFFIC_CAPTURES = [
     # R-MAT scale 22, one launch of 1,520 trees: 880.0 GB read + 340.4 GB written
-    {"applies_to": ["rmat22"], "sha1": "c13cbf502cc0cd4713b848dbbcea358a404c9d20",
+    {"applies_to": ["rmat22"], "sha1": "4dee73ea4277d3ff626fbb56c33c09095703f288",
      "bytes_per_vertex_tree": 1220.36e9 / (1520 * 2394915)},
 ]
 SAMPLER_SOURCES = ("ust_wilson.cu", "ust_relabel.cu")
@@ -103,13 +103,24 @@ def sampler_kernel(n: int) -> str:
     return "sample_aggregate_smem_kernel" if n <= 0xFFFF else "sample_aggregate_large_kernel"
 
 
+def code_of(text: str) -> str:
+    """C++ source without its comments and blank lines (what a capture's
+    validity depends on)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def sampler_sha1():
-    """sha1 over the sampler's sources, in SAMPLER_SOURCES order."""
+    """sha1 over the code (comments left out) of the sampler's sources, in
+    SAMPLER_SOURCES order."""
     import hashlib
     h = hashlib.sha1()
     try:
         for name in SAMPLER_SOURCES:
-            h.update(open(os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", name), "rb").read())
+            path = os.path.join(ROOT, "paper_2006_13679_gb300", "csrc", name)
+            h.update(code_of(open(path, encoding="utf-8").read()).encode())
     except OSError:
         return None
     return h.hexdigest()

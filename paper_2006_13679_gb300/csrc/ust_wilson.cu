@@ -188,23 +188,21 @@ constexpr int kThreadsPerSm = 1024;
 //   NXT(v) the stack top, the tree parent at the end (-1 at u), 4 bytes
 //   DEP(v) the stack depth of the top, 4 bytes
 //   CW(v)  64 bits, by phase: (children | in-edges removed by peeling),
-//          (children | round mark), (pending children | summed sizes),
-//          (preorder number | summed sizes)
+//          (pending children | summed sizes), (preorder number | summed sizes)
 //   MK(v)  the round mark of the popping rounds, 4 bytes
 // Kept as separate compact arrays (rather than one record per vertex), the
-// hubs' entries stay in L1 and L2 (measured on R-MAT scale 22: 16-byte
-// records were 3.5% slower than 8-byte arrays). Nothing of a tree sits in
-// shared memory: the kernel leaves the SM's whole 256 KB to L1, which holds
-// the hubs' entries (measured: keeping the CW words of the 28,672 vertices
-// of largest degree in shared memory instead was 14% slower on R-MAT scale
-// 22 and 22% slower on a 2^20-vertex hyperbolic graph). A single graph is
-// relabelled for the sampler so that the vertices of largest degree come
-// first, their entries side by side in few cache lines: a uniformly drawn
-// neighbour, and so most random successor, counter and ancestor accesses,
-// lands on them (on R-MAT scale 22 the 28,672 highest-degree vertices, 1.2%
-// of them, take 55% of the first draws). The relabelling keeps every row in
-// the input order and every draw keyed by the input id (gd.orig), so the
-// trees are unchanged.
+// entries one step touches share cache lines (measured on R-MAT scale 22:
+// 16-byte records of NXT, DEP and CW were 11% slower). Of a tree only the
+// preorder chunk sits in shared memory: the rest of the SM's on-chip memory
+// is L1 (measured: keeping the CW words of the 28,672 vertices of largest
+// degree in shared memory instead was 14% slower on R-MAT scale 22 and 22%
+// slower on a 2^20-vertex hyperbolic graph). A single graph is relabelled for
+// the sampler in Cuthill-McKee order from the pivot (ust_relabel.cu), so that
+// neighbours, whose entries walks, peeling, sizes and Algorithm 2 touch one
+// after the other, sit in nearby cache lines; its pendant vertices come last
+// and stay out of the trees (GraphDesc::ncore). The relabelling keeps every
+// row in the input order and every draw keyed by the input id (gd.orig), so
+// the trees are unchanged.
 //
 // Phases per tree (one CTA per tree, CTA barriers only):
 //  1. first draws, in-degrees into CW (high words);

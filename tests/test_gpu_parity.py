@@ -261,9 +261,8 @@ def test_counts_above_shared_memory_limit(pkg, orc, maker):
 
 @pytest.mark.parametrize("bt,cps", [(512, 1), (512, 2), (1024, 1)])
 def test_large_sampler_shapes_agree(pkg, orc, bt, cps):
-    """The large-graph sampler at every shape the launch tuner may pick (its
-    shared-memory hot set shrinks with the threads per CTA): R and the draws
-    bit-exact."""
+    """The large-graph sampler at every shape the launch tuner may pick: R
+    and the draws bit-exact."""
     g = synth.rmat(17, 8, seed=2)
     u = synth.max_degree_vertex(g)
     with make(pkg, g, u, block_threads=bt, ctas_per_sm=cps) as h:
