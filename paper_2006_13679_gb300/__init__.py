@@ -34,11 +34,14 @@ def _is_torch(x) -> bool:
 
 
 def _ptr(x, dtype):
-    """(pointer, on_device) for a numpy array or a torch CUDA tensor."""
+    """(pointer, on_device) for a numpy array or a contiguous torch tensor (a
+    CPU tensor, pinned or not, is a host buffer; a CUDA tensor a device one)."""
     if _is_torch(x):
-        if not x.is_cuda or not x.is_contiguous():
-            raise ValueError("device arguments must be contiguous CUDA tensors")
-        return ctypes.c_void_p(x.data_ptr()), 1
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
+        if x.element_size() != np.dtype(dtype).itemsize:
+            raise TypeError(f"expected {np.dtype(dtype).name} elements")
+        return ctypes.c_void_p(x.data_ptr()), (1 if x.is_cuda else 0)
     a = np.ascontiguousarray(x)
     if a.dtype != dtype:
         raise TypeError(f"expected {np.dtype(dtype).name}, got {a.dtype}")
