@@ -124,7 +124,9 @@ typedef struct {
     int32_t n, nnz, pivot, ecc;
     int64_t trees;          /* trees aggregated into R so far, ids [0, trees) */
     uint64_t seed;          /* seed of the last sampling call */
-    int64_t draws;          /* stack entries drawn over all trees (Wilson walk steps) */
+    int64_t draws;          /* stack entries drawn over all trees (Wilson walk steps), counted as
+                               for the whole graph also where the sampler leaves degree-1 vertices
+                               out of its trees */
     int64_t pop_rounds;     /* cycle-popping rounds summed over trees */
     int32_t max_pop_rounds; /* largest number of rounds one tree needed */
     int32_t max_round_pops; /* most vertices popped in one cycle-popping round */

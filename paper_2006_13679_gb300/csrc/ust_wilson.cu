@@ -262,7 +262,7 @@ __device__ __noinline__ int2 core_entry_of(const int32_t *__restrict__ rp, const
                                            uint32_t tree, int ncore)
 {
     const int b = __ldg(rp + x), deg = __ldg(rp + x + 1) - b;
-    const uint32_t lim = k + 64u * (uint32_t)deg + 1024u;
+    const uint32_t lim = (uint32_t)min(k + 64ull * (unsigned long long)deg + 1024ull, 0xFFFFFFFFull);
     for (;;) {
         const unsigned long long r = philox_x64((uint32_t)o, k, tree, graph, key0, key1);
         const int y = __ldg(ci + b + (int)__umul64hi(r, (unsigned long long)deg));
