@@ -39,8 +39,8 @@ enum : int {
 // launch reads one per work item.
 struct GraphDesc {
     int n, u;
-    // The large-graph sampler builds trees on sampler ids below ncore only
-    // (n: all of them). The ids from ncore on are pendant vertices (degree
+    // The samplers build trees on sampler ids below ncore only (n: all of
+    // them). The ids from ncore on are pendant vertices (degree
     // 1, not the pivot): every spanning tree hangs each from its one
     // neighbour, a draw of one by a core vertex closes a 2-cycle that is
     // popped at once (the core vertex takes its next stack entry), and its
@@ -51,17 +51,16 @@ struct GraphDesc {
     long long tree_begin;      // first tree id of the graph in this launch
     const int32_t *rp, *ci, *bpar, *path, *pathptr;
     // entry p of the flattened BFS paths is the edge (path[p], pchild[p]) on
-    // P(powner[p]); fc = f^c(u) entries
+    // P(powner[p]); fc entries (f^c(u), or the core's when ncore < n)
     const int32_t *pchild, *powner;
     int fc;
     long long aoff;  // offset of the graph's arcs in batch-wide arc arrays
-    // Graphs relabelled for the large-graph sampler (single graphs above
-    // kTierMaxVertices): rp / ci / u / path / pathptr are in sampler ids (the
-    // path of sampler vertex v at pathptr[v], listed in sampler order),
-    // orig[v] is the input id of sampler vertex v (Philox counters, outputs)
-    // and rp_in the input row_ptr (arc counts). NULL: ids are input ids.
-    // (bpar, pchild and powner stay in input ids; the large-graph sampler
-    // does not read them.)
+    // Relabelled graphs (single-graph contexts): rp / ci / u / path / pchild
+    // / powner / pathptr are in sampler ids (the path of sampler vertex v at
+    // pathptr[v], the paths listed in sampler order), orig[v] is the input id
+    // of sampler vertex v (Philox counters, outputs) and rp_in the input
+    // row_ptr (arc counts). NULL: ids are input ids (batches). bpar stays in
+    // input ids; the samplers do not read it.
     const int32_t *orig, *rp_in;
 };
 
@@ -165,10 +164,10 @@ struct Ctx {
     // ust_reset until it succeeds. Every sampling call refuses to run then.
     bool ready = false;
 
-    // The large-graph sampler's view of a single graph above
-    // kTierMaxVertices vertices (plain Wilson): vertex ids relabelled in
-    // Cuthill-McKee order from the pivot of ust_init; every row keeps its
-    // input order. B_u, the solve and all outputs stay in input ids.
+    // The samplers' view of a single graph (plain Wilson): vertex ids
+    // relabelled in Cuthill-McKee order from the pivot of ust_init, pendant
+    // vertices last; every row keeps its input order. B_u, the solve and
+    // all outputs stay in input ids.
     bool relabel = false;
     int32_t *d_srp = nullptr, *d_sci = nullptr;     // relabelled CSR
     int32_t *d_orig = nullptr, *d_newid = nullptr;  // sampler id -> input id, and back
