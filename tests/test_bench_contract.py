@@ -55,3 +55,26 @@ def test_per_class_bounds_match_the_library():
     bounds = tuple(int(eval(consts.get(t.strip(), t.strip()), {})) for t in body.split(","))
     assert bounds == bench.BATCH_CLASS_MAX_N
     assert len(bounds) == int(consts["kNumClasses"])
+
+
+def test_traffic_capture_follows_the_sampler_code():
+    """The DRAM traffic a capture measured is reported only while the
+    sampler's code (comments left out) hashes as it did then: a comment edit
+    keeps it, a code edit drops it, and other workloads never get it."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sha = bench.sampler_sha1()
+    assert sha is not None
+    caps = [c for c in bench.TRAFFIC_CAPTURES if c["sha1"] == sha and "rmat22" in c["applies_to"]]
+    n, trees = 2394915, 9475
+    t = bench.traffic_per_launch("rmat22", n, trees)
+    if caps:
+        assert t == caps[0]["bytes_per_vertex_tree"] * n * trees
+    else:
+        assert t is None  # the code changed since the capture: no traffic figure
+    assert bench.traffic_per_launch("hyperbolic20", n, trees) is None
+    code = "int a; // one\n/* two\n three */ int b;\n\nint c;  // four\n"
+    assert bench.code_of(code) == "int a;\n int b;\nint c;"
+    assert bench.code_of(code.replace("one", "uno")) == bench.code_of(code)
+    assert bench.code_of(code.replace("int c", "int d")) != bench.code_of(code)
